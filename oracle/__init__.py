@@ -1,0 +1,252 @@
+"""CPU oracle for grid s-t max-flow / min-cut (test infrastructure only).
+
+Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product (the CUDA library and its
+Python binding) never does.
+
+Contents
+  * ``maxflow``          generic digraph max flow in C (Dinic or Edmonds-Karp).
+  * ``grid_solve``       one grid instance, every lambda of its schedule solved
+                         from scratch (Section 2.1's lambda-schedule, no warm
+                         start), returning int64 flow values and uint8 masks of
+                         the maximal source set.
+  * ``grid_solve_many``  many grid (instance, lambda) jobs on a thread pool.
+  * ``brute_force_*``    enumeration of every s-t cut of a graph with at most
+                         16 non-terminal nodes (numpy, exact).
+
+The definitions follow Section 2 of the paper: an s-t cut splits the nodes into
+an s side and a t side, its cost is the total capacity of arcs from the s side
+to the t side, and a minimum cut has least cost; the max-flow value equals it.
+Where several minimum cuts exist this oracle reports the maximal s side (the
+union of all minimising s sides), i.e. every pixel that cannot reach t in the
+residual graph of a maximum flow.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc into oracle/_build/liboracle.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.oracle_maxflow.restype = ctypes.c_int
+            L.oracle_maxflow.argtypes = [ctypes.c_int, ctypes.c_int, _i32p, _i32p, _i64p,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         _i64p, _i64p, _u8p]
+            L.oracle_grid_solve.restype = ctypes.c_int
+            L.oracle_grid_solve.argtypes = [ctypes.c_int, ctypes.c_int] + [_i32p] * 5 + \
+                [ctypes.c_int64, ctypes.c_int, _i64p, _u8p]
+            L.oracle_grid_arcs.restype = ctypes.c_int
+            L.oracle_grid_arcs.argtypes = [ctypes.c_int, ctypes.c_int] + [_i32p] * 5 + \
+                [ctypes.c_int64, _i32p, _i32p, _i64p]
+            pp = ctypes.POINTER(ctypes.c_void_p)
+            L.oracle_grid_solve_jobs.restype = ctypes.c_int
+            L.oracle_grid_solve_jobs.argtypes = [ctypes.c_int, _i32p, _i32p, pp, pp, pp, pp, pp,
+                                                 _i64p, _i64p, pp, ctypes.c_int]
+            _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _c32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ----------------------------------------------------------------------------
+# generic graphs
+# ----------------------------------------------------------------------------
+
+def maxflow(n: int, tail, head, cap, s: int, t: int, algo: str = "dinic"):
+    """Max flow of a digraph.  Returns (value, arc_flow[m] int64, sink_reach[n] uint8)."""
+    tail = _c32(tail)
+    head = _c32(head)
+    cap = np.ascontiguousarray(cap, dtype=np.int64)
+    m = len(tail)
+    val = ctypes.c_int64(0)
+    fl = np.zeros(max(m, 1), dtype=np.int64)
+    reach = np.zeros(n, dtype=np.uint8)
+    rc = lib().oracle_maxflow(n, m, _p(tail, _i32p), _p(head, _i32p), _p(cap, _i64p), s, t,
+                              1 if algo == "ek" else 0, ctypes.byref(val), _p(fl, _i64p),
+                              _p(reach, _u8p))
+    if rc != 0:
+        raise ValueError("oracle_maxflow: bad graph")
+    return int(val.value), fl[:m], reach
+
+
+def grid_arcs(H, W, w_h, w_v, src0, slope, sink, lam):
+    """The oracle's arc list of one grid instance at one lambda: (tail, head, cap),
+    pixel p = y*W + x, s = H*W, t = H*W + 1."""
+    N = H * W
+    tail = np.zeros(6 * N, np.int32)
+    head = np.zeros(6 * N, np.int32)
+    cap = np.zeros(6 * N, np.int64)
+    arrs = [_c32(a).ravel() for a in (w_h, w_v, src0, slope, sink)]
+    m = lib().oracle_grid_arcs(H, W, *[_p(a, _i32p) for a in arrs], int(lam),
+                               _p(tail, _i32p), _p(head, _i32p), _p(cap, _i64p))
+    return tail[:m], head[:m], cap[:m]
+
+
+# ----------------------------------------------------------------------------
+# grid instances
+# ----------------------------------------------------------------------------
+
+def grid_solve(H, W, w_h, w_v, src0, slope, sink, lambdas, algo: str = "dinic"):
+    """Solve one grid instance at every lambda, each from scratch.
+    Returns (flows int64 [m], masks uint8 [m, H, W]); mask = 1 on the s side."""
+    arrs = [_c32(a).ravel() for a in (w_h, w_v, src0, slope, sink)]
+    lambdas = np.asarray(lambdas, dtype=np.int64).ravel()
+    flows = np.zeros(len(lambdas), np.int64)
+    masks = np.zeros((len(lambdas), H, W), np.uint8)
+    for k, lam in enumerate(lambdas):
+        f = ctypes.c_int64(0)
+        mk = masks[k]
+        rc = lib().oracle_grid_solve(H, W, *[_p(a, _i32p) for a in arrs], int(lam),
+                                     1 if algo == "ek" else 0, ctypes.byref(f), _p(mk, _u8p))
+        if rc != 0:
+            raise ValueError("oracle_grid_solve failed")
+        flows[k] = f.value
+    return flows, masks
+
+
+def grid_solve_many(jobs, n_threads: int | None = None):
+    """jobs: list of (H, W, w_h, w_v, src0, slope, sink, lambda).  Solves them on
+    a pool of ``n_threads`` threads (default: all cores).  Returns (flows int64
+    [n], list of uint8 [H, W] masks)."""
+    n = len(jobs)
+    if n_threads is None:
+        n_threads = os.cpu_count() or 1
+    keep = []
+    Hs = np.array([j[0] for j in jobs], np.int32)
+    Ws = np.array([j[1] for j in jobs], np.int32)
+    ptrs = [(ctypes.c_void_p * max(n, 1))() for _ in range(6)]
+    masks = []
+    for i, j in enumerate(jobs):
+        for a_i, a in enumerate(j[2:7]):
+            a = _c32(a).ravel()
+            keep.append(a)
+            ptrs[a_i][i] = a.ctypes.data
+        mk = np.zeros((j[0], j[1]), np.uint8)
+        masks.append(mk)
+        ptrs[5][i] = mk.ctypes.data
+    lam = np.array([j[7] for j in jobs], np.int64)
+    flows = np.zeros(max(n, 1), np.int64)
+    rc = lib().oracle_grid_solve_jobs(n, _p(Hs, _i32p), _p(Ws, _i32p), *ptrs[:5],
+                                      _p(lam, _i64p), _p(flows, _i64p), ptrs[5], int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_grid_solve_jobs failed")
+    return flows[:n], masks
+
+
+def solve_workload(wl, n_threads: int | None = None, instances=None):
+    """Every (instance, lambda) of a Workload, from scratch.  Returns a list
+    (per instance) of (flows [m], masks [m, H, W])."""
+    idx = list(range(len(wl.instances))) if instances is None else list(instances)
+    jobs, owner = [], []
+    for i in idx:
+        inst = wl.instances[i]
+        im = wl.images[inst.image]
+        for k, lam in enumerate(inst.lambdas):
+            jobs.append((im.H, im.W, im.w_h, im.w_v, inst.src0, inst.slope, inst.sink, int(lam)))
+            owner.append((i, k))
+    flows, masks = grid_solve_many(jobs, n_threads)
+    out = {}
+    for (i, k), f, m in zip(owner, flows, masks):
+        out.setdefault(i, {})[k] = (int(f), m)
+    res = []
+    for i in idx:
+        m = len(wl.instances[i].lambdas)
+        res.append((np.array([out[i][k][0] for k in range(m)], np.int64),
+                    np.stack([out[i][k][1] for k in range(m)])))
+    return res
+
+
+# ----------------------------------------------------------------------------
+# brute force (at most 16 non-terminal nodes)
+# ----------------------------------------------------------------------------
+
+def brute_force_graph(n: int, tail, head, cap, s: int, t: int):
+    """Enumerate every s-t cut of a digraph whose non-terminal nodes number at
+    most 16.  Returns (min cost, union of all minimising s sides as a uint8
+    vector over nodes, number of minimising s sides)."""
+    others = [u for u in range(n) if u != s and u != t]
+    k = len(others)
+    assert k <= 16, "brute force is limited to 16 non-terminal nodes"
+    subsets = np.arange(1 << k, dtype=np.int64)
+    side = np.zeros((n, 1 << k), dtype=np.int64)      # 1 = node on the s side
+    side[s, :] = 1
+    for bit, u in enumerate(others):
+        side[u, :] = (subsets >> bit) & 1
+    tail = np.asarray(tail, np.int64)
+    head = np.asarray(head, np.int64)
+    cap = np.asarray(cap, np.int64)
+    cost = np.zeros(1 << k, dtype=np.int64)
+    for u, v, c in zip(tail, head, cap):
+        if c:
+            cost += c * side[u] * (1 - side[v])
+    best = int(cost.min())
+    arg = np.nonzero(cost == best)[0]
+    union = np.zeros(n, np.uint8)
+    for bit, u in enumerate(others):
+        union[u] = 1 if np.any((arg >> bit) & 1) else 0
+    union[s] = 1
+    return best, union, len(arg)
+
+
+def brute_force_grid(H, W, w_h, w_v, src0, slope, sink, lam):
+    """Brute-force min cut of a grid instance with H*W <= 16, its cut cost
+    written straight from the definition of Section 2 (pairwise edges counted
+    in the direction s side -> t side, terminal edges s->p for t-side pixels
+    and p->t for s-side pixels).  Returns (min cost, maximal s-side mask [H, W],
+    number of minimising sets)."""
+    N = H * W
+    assert N <= 16
+    w_h = np.asarray(w_h, np.int64).reshape(H, W)
+    w_v = np.asarray(w_v, np.int64).reshape(H, W)
+    cs = (np.asarray(src0, np.int64) + np.asarray(slope, np.int64) * int(lam)).reshape(H, W)
+    ct = np.asarray(sink, np.int64).reshape(H, W)
+    S = np.arange(1 << N, dtype=np.int64)
+    on = np.stack([(S >> p) & 1 for p in range(N)]).reshape(H, W, -1)   # 1 = s side
+    cost = (cs[..., None] * (1 - on)).sum(axis=(0, 1)) + (ct[..., None] * on).sum(axis=(0, 1))
+    # horizontal neighbours: an edge of capacity w in each direction
+    a, b = on[:, :-1], on[:, 1:]
+    cost += (w_h[:, :-1, None] * (a * (1 - b) + b * (1 - a))).sum(axis=(0, 1))
+    a, b = on[:-1, :], on[1:, :]
+    cost += (w_v[:-1, :, None] * (a * (1 - b) + b * (1 - a))).sum(axis=(0, 1))
+    best = int(cost.min())
+    arg = np.nonzero(cost == best)[0]
+    union = np.zeros(N, np.uint8)
+    for p in range(N):
+        union[p] = 1 if np.any((arg >> p) & 1) else 0
+    return best, union.reshape(H, W), len(arg)
