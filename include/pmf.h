@@ -1,0 +1,188 @@
+/*
+ * pmf.h - batched parametric maximum flow / minimum cut on 4-connected image
+ * grids, CUDA (sm_103a).
+ *
+ * The problem (Section 2 of "A Parallel Framework for Parametric Maximum Flow
+ * Problems in Image Segmentation", Olaru, Florea, Sminchisescu): every pixel p
+ * of an H x W image is a node joined to the source s by an arc of capacity
+ * cs(p), to the sink t by an arc of capacity ct(p), and to each of its up /
+ * down / left / right neighbours q by arcs p->q and q->p of capacity w(p,q).
+ * A minimum s-t cut splits the pixels into a foreground (s) side and a
+ * background (t) side at least cost; its cost equals the maximum flow value.
+ *
+ * Parametric form (Section 2.1): cs(p, lambda) = src0(p) + slope(p) * lambda
+ * with slope >= 0, solved for a nondecreasing lambda schedule.  The minimum
+ * cuts are then nested and the flow of lambda_k is a valid start for
+ * lambda_{k+1} (Gallo-Grigoriadis-Tarjan, cited in Sections 2.1 and 3).
+ *
+ * Batching (Section 3.1, "supergraphs"): the paper knits many (seed, lambda)
+ * problems into one graph so that one solver call fills the GPU; the minimum
+ * cut of the union decomposes into the minimum cuts of the parts.  Here a
+ * batch holds many independent instances (one instance = one image with one
+ * set of terminal capacities and its own lambda schedule) that are solved in
+ * one persistent launch without any knitting vertices.
+ *
+ * Outputs per solve (instance, lambda_k): the maximum flow value (int64) and a
+ * uint8 mask of the MAXIMAL source set: mask[p] = 1 iff pixel p cannot reach t
+ * in the residual graph of a maximum flow; this set is the union of the s
+ * sides of all minimum cuts.  Both outputs are unique, so the results do not
+ * depend on how the GPU schedules its work.
+ *
+ * Conventions
+ *   - Every call returns a pmf_status and never aborts or traps.
+ *   - Images are row-major int32 arrays of H*W elements, pixel (y, x) at
+ *     index y*W + x.
+ *   - Input pointers are borrowed: the library reads them inside the call or
+ *     in stream order on the batch's stream; host buffers must stay valid
+ *     until pmf_sync returns.
+ *   - The caller owns the device workspace (e.g. a torch tensor) and every
+ *     output buffer.  The library owns the opaque pmf_batch and a few small
+ *     pinned host buffers it allocates in pmf_create_batch.
+ *   - Capacities are integers: 0 <= w <= PMF_MAX_PAIRWISE, 0 <= ct <= PMF_INF,
+ *     0 <= src0 + slope*lambda <= PMF_INF for every lambda of the schedule.
+ *     All arithmetic is exact (int32 state, int64 flow values).
+ */
+#ifndef PMF_H
+#define PMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PMF_API __attribute__((visibility("default")))
+#else
+#define PMF_API
+#endif
+
+#define PMF_INF (1 << 30)                 /* largest terminal capacity ("infinite") */
+#define PMF_MAX_PAIRWISE ((1 << 28) - 1)  /* largest pairwise capacity */
+
+typedef enum {
+    PMF_OK = 0,
+    PMF_ERR_INVALID_ARG = 1,    /* bad pointer, index, size or negative capacity */
+    PMF_ERR_OUT_OF_MEMORY = 2,  /* workspace smaller than pmf_workspace_size() */
+    PMF_ERR_NOT_MONOTONE = 3,   /* decreasing lambda schedule or negative slope */
+    PMF_ERR_OVERFLOW = 4,       /* a capacity above PMF_INF / PMF_MAX_PAIRWISE */
+    PMF_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+    PMF_ERR_NOT_CONVERGED = 6,  /* the device watchdog stopped this instance */
+    PMF_ERR_NOT_READY = 7       /* results requested before a finished solve */
+} pmf_status;
+
+typedef struct pmf_batch pmf_batch;     /* opaque, owned by the library */
+
+/* Batch shape.  All arrays are host arrays, read during the call. */
+typedef struct {
+    int32_t n_images;
+    const int32_t *img_h;       /* [n_images] rows H >= 1 */
+    const int32_t *img_w;       /* [n_images] cols W >= 1 */
+    int32_t n_inst;
+    const int32_t *inst_image;  /* [n_inst] image index of each instance */
+    int32_t max_lambdas;        /* largest schedule length solved by this batch */
+    int32_t device;             /* CUDA device ordinal */
+} pmf_batch_desc;
+
+/* Solver knobs (pmf_set_tuning).  Zero fields keep the default. */
+typedef struct {
+    int32_t tile_h;          /* rows per tile, 4 or 8 (tiles are 32 px wide); default 8 */
+    int32_t sweeps;          /* push/relabel sweeps per tile visit; default 8 */
+    int32_t relabel_every;   /* global relabel after relabel_every * n_tiles(instance)
+                                push/relabel tile visits, in percent of n_tiles;
+                                default 200 (= 2 visits per tile) */
+    int32_t max_visits_per_tile; /* watchdog: an instance stops with
+                                PMF_ERR_NOT_CONVERGED after this many visits per
+                                tile per lambda step on average; default 2000 */
+    int32_t mode;            /* 0 = one persistent launch fed by the device queue
+                                (default); 1 = host-polled rounds, one launch per
+                                round (the per-solve-launch baseline) */
+    int32_t blocks_per_sm;   /* persistent grid = blocks_per_sm * SMs; default: occupancy */
+    int32_t use_graph;       /* 1 = replay the solve as a captured CUDA graph (default 1;
+                                ignored in mode 1) */
+    int32_t reserved;
+} pmf_tuning;
+
+/* Per-instance counters of the last solve (pmf_get_stats). */
+typedef struct {
+    int64_t pr_visits;       /* push/relabel tile visits */
+    int64_t bfs_visits;      /* global-relabel (BFS) tile visits */
+    int64_t global_relabels; /* BFS epochs */
+    int32_t lambdas_done;    /* schedule entries solved */
+    int32_t status;          /* pmf_status of the instance */
+} pmf_stats;
+
+/* Bytes of device workspace a batch of this shape needs (host-only call). */
+PMF_API pmf_status pmf_workspace_size(const pmf_batch_desc *desc, size_t *bytes);
+
+/* Create a batch over a caller-owned device workspace of at least
+ * pmf_workspace_size() bytes (256-byte aligned).  cuda_stream (a cudaStream_t,
+ * may be NULL for the legacy default stream) orders the set-up copies.
+ * PMF_ERR_OUT_OF_MEMORY if the workspace is too small. */
+PMF_API pmf_status pmf_create_batch(const pmf_batch_desc *desc, void *dev_workspace, size_t bytes,
+                            void *cuda_stream, pmf_batch **out);
+
+/* Solver knobs; takes effect at the next pmf_solve_schedule. */
+PMF_API pmf_status pmf_set_tuning(pmf_batch *b, const pmf_tuning *t);
+PMF_API pmf_status pmf_get_tuning(const pmf_batch *b, pmf_tuning *t);
+
+/* Pairwise capacities of one image (Section 2: the smoothness edges).
+ * w_h[y*W + x] joins (y,x)-(y,x+1), w_v[y*W + x] joins (y,x)-(y+1,x); the last
+ * column of w_h and the last row of w_v are ignored.  on_device = 1: device
+ * pointers (checked on the device, errors reported by pmf_sync); 0: host
+ * pointers (checked here, PMF_ERR_INVALID_ARG / PMF_ERR_OVERFLOW). */
+PMF_API pmf_status pmf_set_capacities(pmf_batch *b, int32_t image, const int32_t *w_h,
+                              const int32_t *w_v, int on_device);
+
+/* Terminal capacities of one instance (Section 2: the unary edges; Section
+ * 2.1: the lambda-dependent source side).  cs(p, lambda) = src0[p] +
+ * slope[p]*lambda, ct(p) = sink[p].  slope < 0 gives PMF_ERR_NOT_MONOTONE.
+ * on_device as for pmf_set_capacities. */
+PMF_API pmf_status pmf_set_terminals(pmf_batch *b, int32_t inst, const int32_t *src0,
+                             const int32_t *slope, const int32_t *sink, int on_device);
+
+/* Solve every instance at every lambda of its schedule.  lambdas is a host
+ * array [n_inst][n_lambda] (n_lambda <= max_lambdas), nondecreasing along each
+ * row (else PMF_ERR_NOT_MONOTONE, nothing launched).  Asynchronous on
+ * cuda_stream; call pmf_sync before reading results.  lambda_0 starts from the
+ * zero flow; each later lambda keeps the previous flow and labels (GGT warm
+ * start). */
+PMF_API pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_lambda,
+                              void *cuda_stream);
+
+/* Wait for the last solve.  per_instance (host, may be NULL) receives each
+ * instance's pmf_status.  Returns PMF_OK iff every instance converged. */
+PMF_API pmf_status pmf_sync(pmf_batch *b, pmf_status *per_instance);
+
+/* Mask of solve (inst, k): H*W bytes, 1 = source (foreground) side.
+ * on_device = 1: mask is a device pointer (copied in stream order, then the
+ * stream is synchronised), 0: host pointer.  PMF_ERR_NOT_READY before pmf_sync
+ * of a finished solve. */
+PMF_API pmf_status pmf_get_cut(pmf_batch *b, int32_t inst, int32_t k, uint8_t *mask, int on_device);
+
+/* Maximum flow value of solve (inst, k) (Section 2: equal to the minimum cut
+ * cost), after pmf_sync. */
+PMF_API pmf_status pmf_get_flow(pmf_batch *b, int32_t inst, int32_t k, int64_t *flow);
+
+/* Counters of the last solve for one instance, after pmf_sync. */
+PMF_API pmf_status pmf_get_stats(pmf_batch *b, int32_t inst, pmf_stats *out);
+
+/* Device-side pointers of the results, for zero-copy consumers: masks of
+ * instance inst as [max_lambdas][rows][pitch] bytes, rows/pitch returned. */
+PMF_API pmf_status pmf_get_mask_layout(pmf_batch *b, int32_t inst, const uint8_t **dev_masks,
+                               int32_t *rows, int32_t *pitch);
+
+/* Release the host side of the batch (the workspace stays the caller's). */
+PMF_API void pmf_destroy_batch(pmf_batch *b);
+
+PMF_API const char *pmf_status_string(pmf_status s);
+
+/* Library version, e.g. "pmf 0.1.0 sm_103a". */
+PMF_API const char *pmf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMF_H */

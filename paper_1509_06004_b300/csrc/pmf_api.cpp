@@ -1,0 +1,572 @@
+// C ABI of the batched parametric grid max-flow solver (declared in pmf.h).
+// Host-side logic only: argument checks, workspace layout, set-up copies,
+// the solve launch sequence (optionally captured once as a CUDA graph and
+// replayed), and reading back results.  Every step of the solve itself runs in
+// the kernels of pmf_kernels.cu.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "pmf.h"
+#include "pmf_internal.h"
+
+using namespace pmf;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+size_t align_up(size_t v, size_t a = ALIGN) { return (v + a - 1) / a * a; }
+int round_up_i(int v, int a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    size_t img_planes, inst_planes, masks, dev_inst, ist, tiles, tile_inst, ring, lambdas, flows,
+        globals, staging, img_flags, inst_flags, total;
+    size_t ring_cap;
+    size_t max_tiles;
+    size_t max_hw;
+    std::vector<int> rows, pitch;               // per image
+    std::vector<int64_t> img_off;               // per image, int32 elements
+    std::vector<int64_t> plane_off, mask_off;   // per instance
+};
+
+bool desc_ok(const pmf_batch_desc *d) {
+    if (!d || d->n_images < 1 || d->n_inst < 1 || d->max_lambdas < 1) return false;
+    if (!d->img_h || !d->img_w || !d->inst_image) return false;
+    for (int i = 0; i < d->n_images; ++i)
+        if (d->img_h[i] < 1 || d->img_w[i] < 1 || (int64_t)d->img_h[i] * d->img_w[i] > (1 << 28)) return false;
+    for (int i = 0; i < d->n_inst; ++i)
+        if (d->inst_image[i] < 0 || d->inst_image[i] >= d->n_images) return false;
+    return true;
+}
+
+Layout make_layout(const pmf_batch_desc *d) {
+    Layout L;
+    L.rows.resize(d->n_images);
+    L.pitch.resize(d->n_images);
+    L.img_off.resize(d->n_images);
+    size_t img_elems = 0;
+    L.max_hw = 0;
+    for (int i = 0; i < d->n_images; ++i) {
+        L.rows[i] = round_up_i(d->img_h[i], ROW_ALIGN);
+        L.pitch[i] = round_up_i(d->img_w[i], TILE_W);
+        L.img_off[i] = (int64_t)img_elems;
+        img_elems += (size_t)N_IMG_PLANES * L.rows[i] * L.pitch[i];
+        L.max_hw = std::max(L.max_hw, (size_t)d->img_h[i] * d->img_w[i]);
+    }
+    L.plane_off.resize(d->n_inst);
+    L.mask_off.resize(d->n_inst);
+    size_t inst_elems = 0, mask_bytes = 0;
+    L.max_tiles = 0;
+    for (int i = 0; i < d->n_inst; ++i) {
+        const int im = d->inst_image[i];
+        const size_t ps = (size_t)L.rows[im] * L.pitch[im];
+        L.plane_off[i] = (int64_t)inst_elems;
+        inst_elems += (size_t)N_INST_PLANES * ps;
+        L.mask_off[i] = (int64_t)mask_bytes;
+        mask_bytes += (size_t)d->max_lambdas * ps;
+        L.max_tiles += (size_t)(L.rows[im] / 4) * (L.pitch[im] / TILE_W);   // smallest tile height
+    }
+    L.ring_cap = 1;
+    while (L.ring_cap < L.max_tiles) L.ring_cap <<= 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes); return o; };
+    L.img_planes = take(img_elems * 4);
+    L.inst_planes = take(inst_elems * 4);
+    L.masks = take(mask_bytes);
+    L.dev_inst = take(sizeof(DevInst) * d->n_inst);
+    L.ist = take(sizeof(InstState) * d->n_inst);
+    L.tiles = take(sizeof(TileState) * L.max_tiles);
+    L.tile_inst = take(sizeof(int32_t) * L.max_tiles);
+    L.ring = take(sizeof(int32_t) * L.ring_cap);
+    L.lambdas = take(sizeof(int32_t) * (size_t)d->n_inst * d->max_lambdas);
+    L.flows = take(sizeof(int64_t) * (size_t)d->n_inst * d->max_lambdas);
+    L.globals = take(sizeof(Globals));
+    L.staging = take(sizeof(int32_t) * 3 * L.max_hw);
+    L.img_flags = take(sizeof(int32_t) * d->n_images);
+    L.inst_flags = take(sizeof(int32_t) * d->n_inst);
+    L.total = off;
+    return L;
+}
+
+struct DeviceGuard {
+    int old = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&old) != cudaSuccess) old = -1;
+        if (old != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (old >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != old) cudaSetDevice(old);
+    }
+};
+
+}  // namespace
+
+struct pmf_batch {
+    pmf_batch_desc desc{};
+    std::vector<int32_t> img_h, img_w, inst_image;
+    Layout L;
+    char *ws = nullptr;
+    Params P{};
+    pmf_tuning tune{};
+    int n_sm = 0;
+    int device = 0;
+    cudaStream_t setup_stream = nullptr;   // caller's stream for set-up copies
+    cudaStream_t cap_stream = nullptr;     // private stream used for graph capture
+    cudaEvent_t done = nullptr;
+    bool in_flight = false;
+    bool solved = false;
+    int32_t last_n_lambda = 0;
+    std::vector<DevInst> dinst;            // host copy of the descriptors
+    // pinned host mirrors
+    int32_t *lam_h = nullptr;
+    InstState *ist_h = nullptr;
+    long long *flows_h = nullptr;
+    Globals *glob_h = nullptr;
+    DevInst *dinst_h = nullptr;
+    // captured graph
+    cudaGraphExec_t gexec = nullptr;
+    int graph_n_lambda = -1;
+    int graph_key = -1;
+    int worker_grid = 0;
+};
+
+namespace {
+
+pmf_status cuda_err(cudaError_t e) { return e == cudaSuccess ? PMF_OK : PMF_ERR_CUDA; }
+
+void apply_defaults(pmf_tuning *t) {
+    if (t->tile_h != 4 && t->tile_h != 8) t->tile_h = 8;
+    if (t->sweeps <= 0) t->sweeps = 8;
+    if (t->relabel_every <= 0) t->relabel_every = 200;
+    if (t->max_visits_per_tile <= 0) t->max_visits_per_tile = 2000;
+    if (t->mode != 1) t->mode = 0;
+    if (t->use_graph != 0) t->use_graph = 1;
+}
+
+// per-instance tile geometry for the current tile height; uploads the table
+pmf_status refresh_geometry(pmf_batch *b, cudaStream_t s) {
+    const int th = b->tune.tile_h;
+    int base = 0;
+    for (int i = 0; i < b->desc.n_inst; ++i) {
+        const int im = b->inst_image[i];
+        DevInst &d = b->dinst[i];
+        d.H = b->img_h[im];
+        d.W = b->img_w[im];
+        d.rows = b->L.rows[im];
+        d.pitch = b->L.pitch[im];
+        d.image = im;
+        d.tiles_x = d.pitch / TILE_W;
+        d.tiles_y = d.rows / th;
+        d.n_tiles = d.tiles_x * d.tiles_y;
+        d.tile_base = base;
+        base += d.n_tiles;
+        d.hcap = d.H * d.W + 1;
+        d.plane_off = b->L.plane_off[i];
+        d.img_off = b->L.img_off[im];
+        d.mask_off = b->L.mask_off[i];
+        b->dinst_h[i] = d;
+    }
+    b->P.n_tiles_total = base;
+    b->P.tile_h = th;
+    return cuda_err(cudaMemcpyAsync(b->ws + b->L.dev_inst, b->dinst_h, sizeof(DevInst) * b->desc.n_inst,
+                                    cudaMemcpyHostToDevice, s));
+}
+
+int grid_size(pmf_batch *b) {
+    int bps = b->tune.blocks_per_sm;
+    if (bps <= 0) {
+        if (worker_occupancy(b->tune.tile_h, &bps) != cudaSuccess || bps <= 0) bps = 4;
+    }
+    return bps * b->n_sm;
+}
+
+// the launch sequence of one solve (persistent mode)
+pmf_status enqueue_solve(pmf_batch *b, int n_lambda, cudaStream_t s) {
+    const size_t lam_bytes = sizeof(int32_t) * (size_t)b->desc.n_inst * b->desc.max_lambdas;
+    cudaError_t e = cudaMemcpyAsync(b->ws + b->L.lambdas, b->lam_h, lam_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_reset(b->P, s);
+    int maxpix = 0;
+    for (int i = 0; i < b->desc.n_inst; ++i) maxpix = std::max(maxpix, b->dinst[i].rows * b->dinst[i].pitch);
+    if (e == cudaSuccess) e = launch_init(b->P, maxpix, s);
+    if (e == cudaSuccess) e = launch_worker(b->P, b->worker_grid, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->ist_h, b->ws + b->L.ist, sizeof(InstState) * b->desc.n_inst, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->flows_h, b->ws + b->L.flows, sizeof(long long) * (size_t)b->desc.n_inst * b->desc.max_lambdas,
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->glob_h, b->ws + b->L.globals, sizeof(Globals), cudaMemcpyDeviceToHost, s);
+    (void)n_lambda;
+    return cuda_err(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pmf_version(void) { return "pmf 0.1.0 sm_103a"; }
+
+const char *pmf_status_string(pmf_status s) {
+    switch (s) {
+        case PMF_OK: return "ok";
+        case PMF_ERR_INVALID_ARG: return "invalid argument";
+        case PMF_ERR_OUT_OF_MEMORY: return "workspace too small";
+        case PMF_ERR_NOT_MONOTONE: return "lambda schedule decreasing or negative slope";
+        case PMF_ERR_OVERFLOW: return "capacity above the supported maximum";
+        case PMF_ERR_CUDA: return "CUDA runtime error";
+        case PMF_ERR_NOT_CONVERGED: return "watchdog stopped the solve";
+        case PMF_ERR_NOT_READY: return "no finished solve";
+    }
+    return "unknown status";
+}
+
+pmf_status pmf_workspace_size(const pmf_batch_desc *desc, size_t *bytes) {
+    if (!desc_ok(desc) || !bytes) return PMF_ERR_INVALID_ARG;
+    *bytes = make_layout(desc).total;
+    return PMF_OK;
+}
+
+pmf_status pmf_create_batch(const pmf_batch_desc *desc, void *dev_workspace, size_t bytes,
+                            void *cuda_stream, pmf_batch **out) {
+    if (!out) return PMF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!desc_ok(desc) || !dev_workspace) return PMF_ERR_INVALID_ARG;
+    if (((uintptr_t)dev_workspace) % ALIGN) return PMF_ERR_INVALID_ARG;
+    Layout L = make_layout(desc);
+    if (bytes < L.total) return PMF_ERR_OUT_OF_MEMORY;
+    DeviceGuard dg(desc->device);
+    pmf_batch *b = new (std::nothrow) pmf_batch();
+    if (!b) return PMF_ERR_OUT_OF_MEMORY;
+    b->desc = *desc;
+    b->img_h.assign(desc->img_h, desc->img_h + desc->n_images);
+    b->img_w.assign(desc->img_w, desc->img_w + desc->n_images);
+    b->inst_image.assign(desc->inst_image, desc->inst_image + desc->n_inst);
+    b->desc.img_h = b->img_h.data();
+    b->desc.img_w = b->img_w.data();
+    b->desc.inst_image = b->inst_image.data();
+    b->L = L;
+    b->ws = (char *)dev_workspace;
+    b->device = desc->device;
+    b->setup_stream = (cudaStream_t)cuda_stream;
+    b->dinst.resize(desc->n_inst);
+    apply_defaults(&b->tune);
+    cudaError_t e = cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
+    const size_t nl = (size_t)desc->n_inst * desc->max_lambdas;
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->lam_h, sizeof(int32_t) * nl, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->ist_h, sizeof(InstState) * desc->n_inst, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->flows_h, sizeof(long long) * nl, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->glob_h, sizeof(Globals), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->dinst_h, sizeof(DevInst) * desc->n_inst, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        pmf_destroy_batch(b);
+        return PMF_ERR_CUDA;
+    }
+    Params &P = b->P;
+    P.planes = (int32_t *)(b->ws + L.inst_planes);
+    P.img = (const int32_t *)(b->ws + L.img_planes);
+    P.masks = (uint8_t *)(b->ws + L.masks);
+    P.inst = (const DevInst *)(b->ws + L.dev_inst);
+    P.ist = (InstState *)(b->ws + L.ist);
+    P.tiles = (TileState *)(b->ws + L.tiles);
+    P.tile_inst = (const int32_t *)(b->ws + L.tile_inst);
+    P.ring = (int32_t *)(b->ws + L.ring);
+    P.lambdas = (const int32_t *)(b->ws + L.lambdas);
+    P.flows = (long long *)(b->ws + L.flows);
+    P.g = (Globals *)(b->ws + L.globals);
+    P.img_flags = (const int32_t *)(b->ws + L.img_flags);
+    P.inst_flags = (int32_t *)(b->ws + L.inst_flags);
+    P.ring_mask = (unsigned long long)(L.ring_cap - 1);
+    P.n_inst = desc->n_inst;
+    P.max_lambdas = desc->max_lambdas;
+    P.stall_ns = 5000000000LL;
+    P.max_ns = 120000000000LL;
+    if (const char *ev = getenv("PMF_MAX_SECONDS")) {
+        const double sec = atof(ev);
+        if (sec > 0) P.max_ns = (long long)(sec * 1e9);
+    }
+    // zero the parts that are read before being written: planes (capacities
+    // not set stay zero), flags
+    cudaStream_t s = b->setup_stream;
+    e = cudaMemsetAsync(b->ws + L.img_planes, 0, L.masks - L.img_planes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ws + L.img_flags, 0, L.total - L.img_flags, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ws + L.globals, 0, sizeof(Globals), s);
+    if (e == cudaSuccess) {
+        const pmf_status st = refresh_geometry(b, s);
+        if (st != PMF_OK) e = cudaErrorUnknown;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        pmf_destroy_batch(b);
+        return PMF_ERR_CUDA;
+    }
+    *out = b;
+    return PMF_OK;
+}
+
+pmf_status pmf_set_tuning(pmf_batch *b, const pmf_tuning *t) {
+    if (!b || !t) return PMF_ERR_INVALID_ARG;
+    if (t->tile_h != 0 && t->tile_h != 4 && t->tile_h != 8) return PMF_ERR_INVALID_ARG;
+    if (t->sweeps < 0 || t->relabel_every < 0 || t->max_visits_per_tile < 0 || t->blocks_per_sm < 0)
+        return PMF_ERR_INVALID_ARG;
+    if (b->in_flight) {
+        DeviceGuard dg(b->device);
+        cudaEventSynchronize(b->done);
+        b->in_flight = false;
+    }
+    pmf_tuning n = *t;
+    apply_defaults(&n);
+    b->tune = n;
+    b->graph_key = -1;   // re-capture on next solve
+    return PMF_OK;
+}
+
+pmf_status pmf_get_tuning(const pmf_batch *b, pmf_tuning *t) {
+    if (!b || !t) return PMF_ERR_INVALID_ARG;
+    *t = b->tune;
+    return PMF_OK;
+}
+
+pmf_status pmf_set_capacities(pmf_batch *b, int32_t image, const int32_t *w_h, const int32_t *w_v,
+                              int on_device) {
+    if (!b || !w_h || !w_v || image < 0 || image >= b->desc.n_images) return PMF_ERR_INVALID_ARG;
+    DeviceGuard dg(b->device);
+    if (b->in_flight) { cudaEventSynchronize(b->done); b->in_flight = false; }
+    const int H = b->img_h[image], W = b->img_w[image];
+    const size_t n = (size_t)H * W;
+    cudaStream_t s = b->setup_stream;
+    const int32_t *src_h = w_h, *src_v = w_v;
+    if (!on_device) {
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int32_t a = (x < W - 1) ? w_h[(size_t)y * W + x] : 0;
+                const int32_t c = (y < H - 1) ? w_v[(size_t)y * W + x] : 0;
+                if (a < 0 || c < 0) return PMF_ERR_INVALID_ARG;
+                if (a > PMF_MAX_PAIRWISE || c > PMF_MAX_PAIRWISE) return PMF_ERR_OVERFLOW;
+            }
+        int32_t *stg = (int32_t *)(b->ws + b->L.staging);
+        cudaError_t e = cudaMemcpyAsync(stg, w_h, n * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(stg + n, w_v, n * 4, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return PMF_ERR_CUDA;
+        src_h = stg;
+        src_v = stg + n;
+    }
+    DevInst d{};
+    d.H = H;
+    d.W = W;
+    d.rows = b->L.rows[image];
+    d.pitch = b->L.pitch[image];
+    d.img_off = b->L.img_off[image];
+    int32_t *flags = (int32_t *)(b->ws + b->L.img_flags) + image;
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = launch_pad_image(b->P, image, d, src_h, src_v, flags, s);
+    b->solved = false;
+    return cuda_err(e);
+}
+
+pmf_status pmf_set_terminals(pmf_batch *b, int32_t inst, const int32_t *src0, const int32_t *slope,
+                             const int32_t *sink, int on_device) {
+    if (!b || !src0 || !slope || !sink || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
+    DeviceGuard dg(b->device);
+    if (b->in_flight) { cudaEventSynchronize(b->done); b->in_flight = false; }
+    const int im = b->inst_image[inst];
+    const int H = b->img_h[im], W = b->img_w[im];
+    const size_t n = (size_t)H * W;
+    cudaStream_t s = b->setup_stream;
+    const int32_t *a = src0, *c = slope, *k = sink;
+    if (!on_device) {
+        for (size_t i = 0; i < n; ++i) {
+            if (slope[i] < 0) return PMF_ERR_NOT_MONOTONE;
+            if (src0[i] < 0 || sink[i] < 0) return PMF_ERR_INVALID_ARG;
+            if (src0[i] > PMF_INF || sink[i] > PMF_INF) return PMF_ERR_OVERFLOW;
+        }
+        int32_t *stg = (int32_t *)(b->ws + b->L.staging);
+        cudaError_t e = cudaMemcpyAsync(stg, src0, n * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(stg + n, slope, n * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(stg + 2 * n, sink, n * 4, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return PMF_ERR_CUDA;
+        a = stg;
+        c = stg + n;
+        k = stg + 2 * n;
+    }
+    DevInst d = b->dinst[inst];
+    cudaError_t e = cudaMemsetAsync((int32_t *)(b->ws + b->L.inst_flags) + inst, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = launch_pad_terminals(b->P, inst, d, a, c, k, s);
+    b->solved = false;
+    return cuda_err(e);
+}
+
+pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_lambda, void *cuda_stream) {
+    if (!b || !lambdas || n_lambda < 1 || n_lambda > b->desc.max_lambdas) return PMF_ERR_INVALID_ARG;
+    for (int i = 0; i < b->desc.n_inst; ++i)
+        for (int k = 1; k < n_lambda; ++k)
+            if (lambdas[(size_t)i * n_lambda + k] < lambdas[(size_t)i * n_lambda + k - 1]) return PMF_ERR_NOT_MONOTONE;
+    DeviceGuard dg(b->device);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (b->in_flight) { cudaEventSynchronize(b->done); b->in_flight = false; }
+    // lambda table [n_inst][max_lambdas] in pinned staging
+    for (int i = 0; i < b->desc.n_inst; ++i)
+        for (int k = 0; k < b->desc.max_lambdas; ++k)
+            b->lam_h[(size_t)i * b->desc.max_lambdas + k] =
+                lambdas[(size_t)i * n_lambda + std::min(k, n_lambda - 1)];
+    b->P.sweeps = b->tune.sweeps;
+    b->P.relabel_pct = b->tune.relabel_every;
+    b->P.max_visits_per_tile = b->tune.max_visits_per_tile;
+    const bool geo_changed = (b->P.tile_h != b->tune.tile_h) || (b->last_n_lambda != n_lambda);
+    if (geo_changed) {
+        // tile geometry and schedule length live in the descriptor table
+        for (int i = 0; i < b->desc.n_inst; ++i) b->dinst[i].n_lambda = n_lambda;
+        const pmf_status st = refresh_geometry(b, s);
+        if (st != PMF_OK) return st;
+        b->last_n_lambda = n_lambda;
+        b->graph_key = -1;
+    }
+    b->worker_grid = grid_size(b);
+    b->solved = false;
+    cudaError_t e = cudaSuccess;
+    if (b->tune.mode == 1) {
+        // host-polled rounds: one worker launch per round, the host reads the
+        // number of pending items after each (the one-call-per-iteration form)
+        const size_t lam_bytes = sizeof(int32_t) * (size_t)b->desc.n_inst * b->desc.max_lambdas;
+        e = cudaMemcpyAsync(b->ws + b->L.lambdas, b->lam_h, lam_bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_reset(b->P, s);
+        int maxpix = 0;
+        for (int i = 0; i < b->desc.n_inst; ++i) maxpix = std::max(maxpix, b->dinst[i].rows * b->dinst[i].pitch);
+        if (e == cudaSuccess) e = launch_init(b->P, maxpix, s);
+        const auto t0 = std::chrono::steady_clock::now();
+        for (long long round = 0; e == cudaSuccess && round < (1LL << 24); ++round) {
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el * 1e9 > (double)b->P.max_ns) break;
+            e = launch_begin_round(b->P, s);
+            if (e == cudaSuccess) e = launch_worker(b->P, b->worker_grid, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(b->glob_h, b->ws + b->L.globals, sizeof(Globals), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess || b->glob_h->pending <= 0 || b->glob_h->err) break;
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->ist_h, b->ws + b->L.ist, sizeof(InstState) * b->desc.n_inst, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->flows_h, b->ws + b->L.flows, sizeof(long long) * (size_t)b->desc.n_inst * b->desc.max_lambdas,
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->glob_h, b->ws + b->L.globals, sizeof(Globals), cudaMemcpyDeviceToHost, s);
+    } else if (b->tune.use_graph) {
+        const int key = b->tune.tile_h * 1000003 + n_lambda * 131 + b->worker_grid;
+        if (b->graph_key != key || !b->gexec) {
+            if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const pmf_status st = enqueue_solve(b, n_lambda, b->cap_stream);
+                const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
+                e = (st != PMF_OK) ? cudaErrorUnknown : e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) { b->gexec = nullptr; return PMF_ERR_CUDA; }
+            b->graph_key = key;
+        }
+        e = cudaGraphLaunch(b->gexec, s);
+    } else {
+        const pmf_status st = enqueue_solve(b, n_lambda, s);
+        if (st != PMF_OK) return st;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->done, s);
+    if (e != cudaSuccess) return PMF_ERR_CUDA;
+    b->in_flight = true;
+    return PMF_OK;
+}
+
+pmf_status pmf_sync(pmf_batch *b, pmf_status *per_instance) {
+    if (!b) return PMF_ERR_INVALID_ARG;
+    DeviceGuard dg(b->device);
+    if (!b->in_flight && !b->solved) return PMF_ERR_NOT_READY;
+    if (b->in_flight) {
+        const cudaError_t e = cudaEventSynchronize(b->done);
+        b->in_flight = false;
+        if (e != cudaSuccess) return PMF_ERR_CUDA;
+        b->solved = true;
+    }
+    pmf_status all = PMF_OK;
+    const bool gerr = b->glob_h->err != 0;
+    for (int i = 0; i < b->desc.n_inst; ++i) {
+        pmf_status st = (pmf_status)b->ist_h[i].status;
+        if (st == PMF_OK && (b->ist_h[i].phase != PH_DONE || b->ist_h[i].k < b->last_n_lambda))
+            st = PMF_ERR_NOT_CONVERGED;
+        if (gerr && st == PMF_OK && b->ist_h[i].phase != PH_DONE) st = PMF_ERR_NOT_CONVERGED;
+        if (per_instance) per_instance[i] = st;
+        if (st != PMF_OK && all == PMF_OK) all = st;
+    }
+    return all;
+}
+
+pmf_status pmf_get_cut(pmf_batch *b, int32_t inst, int32_t k, uint8_t *mask, int on_device) {
+    if (!b || !mask || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
+    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
+    if (k < 0 || k >= b->last_n_lambda) return PMF_ERR_INVALID_ARG;
+    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k <= k) return PMF_ERR_NOT_READY;
+    DeviceGuard dg(b->device);
+    const DevInst &d = b->dinst[inst];
+    const char *src = b->ws + b->L.masks + d.mask_off + (size_t)k * d.rows * d.pitch;
+    cudaError_t e = cudaMemcpy2DAsync(mask, d.W, src, d.pitch, d.W, d.H,
+                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                      b->cap_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap_stream);
+    return cuda_err(e);
+}
+
+pmf_status pmf_get_flow(pmf_batch *b, int32_t inst, int32_t k, int64_t *flow) {
+    if (!b || !flow || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
+    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
+    if (k < 0 || k >= b->last_n_lambda) return PMF_ERR_INVALID_ARG;
+    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k <= k) return PMF_ERR_NOT_READY;
+    *flow = b->flows_h[(size_t)inst * b->desc.max_lambdas + k];
+    return PMF_OK;
+}
+
+pmf_status pmf_get_stats(pmf_batch *b, int32_t inst, pmf_stats *out) {
+    if (!b || !out || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
+    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
+    const InstState &s = b->ist_h[inst];
+    out->pr_visits = (int64_t)s.pr_visits;
+    out->bfs_visits = (int64_t)s.bfs_visits;
+    out->global_relabels = (int64_t)s.epochs;
+    out->lambdas_done = s.k;
+    out->status = s.status;
+    return PMF_OK;
+}
+
+pmf_status pmf_get_mask_layout(pmf_batch *b, int32_t inst, const uint8_t **dev_masks, int32_t *rows,
+                               int32_t *pitch) {
+    if (!b || !dev_masks || !rows || !pitch || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
+    const DevInst &d = b->dinst[inst];
+    *dev_masks = (const uint8_t *)(b->ws + b->L.masks + d.mask_off);
+    *rows = d.rows;
+    *pitch = d.pitch;
+    return PMF_OK;
+}
+
+void pmf_destroy_batch(pmf_batch *b) {
+    if (!b) return;
+    DeviceGuard dg(b->device);
+    if (b->in_flight && b->done) cudaEventSynchronize(b->done);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->lam_h) cudaFreeHost(b->lam_h);
+    if (b->ist_h) cudaFreeHost(b->ist_h);
+    if (b->flows_h) cudaFreeHost(b->flows_h);
+    if (b->glob_h) cudaFreeHost(b->glob_h);
+    if (b->dinst_h) cudaFreeHost(b->dinst_h);
+    delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,327 @@
+"""ctypes binding of libpmf.so (the C ABI declared in include/pmf.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  PyTorch provides the device workspace and the stream.  There is no
+CPU fallback: if the library is missing or no GPU is present the calls raise.
+
+    b = Batch([(H, W)], inst_image=[0, 0], max_lambdas=20)
+    b.set_capacities(0, w_h, w_v)               # numpy (host) or torch.cuda tensors
+    b.set_terminals(0, src0, slope, sink)
+    b.solve(lambdas)                            # [n_inst][n_lambda], nondecreasing rows
+    b.sync()
+    flow = b.get_flow(inst, k); mask = b.get_cut(inst, k)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpmf.so")
+
+PMF_OK = 0
+PMF_ERR_INVALID_ARG = 1
+PMF_ERR_OUT_OF_MEMORY = 2
+PMF_ERR_NOT_MONOTONE = 3
+PMF_ERR_OVERFLOW = 4
+PMF_ERR_CUDA = 5
+PMF_ERR_NOT_CONVERGED = 6
+PMF_ERR_NOT_READY = 7
+PMF_INF = 1 << 30
+PMF_MAX_PAIRWISE = (1 << 28) - 1
+
+# every entry point declared in include/pmf.h
+EXPORTS = ["pmf_workspace_size", "pmf_create_batch", "pmf_set_tuning", "pmf_get_tuning",
+           "pmf_set_capacities", "pmf_set_terminals", "pmf_solve_schedule", "pmf_sync",
+           "pmf_get_cut", "pmf_get_flow", "pmf_get_stats", "pmf_get_mask_layout",
+           "pmf_destroy_batch", "pmf_status_string", "pmf_version"]
+
+
+class PmfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("n_images", ctypes.c_int32), ("img_h", ctypes.POINTER(ctypes.c_int32)),
+                ("img_w", ctypes.POINTER(ctypes.c_int32)), ("n_inst", ctypes.c_int32),
+                ("inst_image", ctypes.POINTER(ctypes.c_int32)), ("max_lambdas", ctypes.c_int32),
+                ("device", ctypes.c_int32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tile_h", ctypes.c_int32), ("sweeps", ctypes.c_int32),
+                ("relabel_every", ctypes.c_int32), ("max_visits_per_tile", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("pr_visits", ctypes.c_int64), ("bfs_visits", ctypes.c_int64),
+                ("global_relabels", ctypes.c_int64), ("lambdas_done", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib(path: str | None = None):
+    """Load libpmf.so (built by ``python -m paper_1509_06004_b300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"libpmf.so not found at {p}; build it with "
+                                   "`python -m paper_1509_06004_b300.build` (no CPU fallback exists)")
+            L = ctypes.CDLL(p)
+            vp = ctypes.c_void_p
+            i32 = ctypes.c_int32
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            L.pmf_workspace_size.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(ctypes.c_size_t)]
+            L.pmf_create_batch.argtypes = [ctypes.POINTER(BatchDesc), vp, ctypes.c_size_t, vp,
+                                           ctypes.POINTER(vp)]
+            L.pmf_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+            L.pmf_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+            L.pmf_set_capacities.argtypes = [vp, i32, vp, vp, ctypes.c_int]
+            L.pmf_set_terminals.argtypes = [vp, i32, vp, vp, vp, ctypes.c_int]
+            L.pmf_solve_schedule.argtypes = [vp, i32p, i32, vp]
+            L.pmf_sync.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+            L.pmf_get_cut.argtypes = [vp, i32, i32, vp, ctypes.c_int]
+            L.pmf_get_flow.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_int64)]
+            L.pmf_get_stats.argtypes = [vp, i32, ctypes.POINTER(Stats)]
+            L.pmf_get_mask_layout.argtypes = [vp, i32, ctypes.POINTER(vp), i32p, i32p]
+            L.pmf_destroy_batch.argtypes = [vp]
+            L.pmf_destroy_batch.restype = None
+            L.pmf_status_string.argtypes = [ctypes.c_int]
+            L.pmf_status_string.restype = ctypes.c_char_p
+            L.pmf_version.argtypes = []
+            L.pmf_version.restype = ctypes.c_char_p
+            for name in EXPORTS:
+                if name not in ("pmf_destroy_batch", "pmf_status_string", "pmf_version"):
+                    getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().pmf_status_string(int(s)).decode()
+    except RuntimeError:
+        return "unknown"
+
+
+def _check(st: int, where: str):
+    if st != PMF_OK:
+        raise PmfError(st, where)
+
+
+def _desc(shapes, inst_image, max_lambdas, device):
+    Hs = np.ascontiguousarray([s[0] for s in shapes], np.int32)
+    Ws = np.ascontiguousarray([s[1] for s in shapes], np.int32)
+    ii = np.ascontiguousarray(inst_image, np.int32)
+    d = BatchDesc(len(shapes), Hs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                  Ws.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(ii),
+                  ii.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(max_lambdas), int(device))
+    return d, (Hs, Ws, ii)
+
+
+def workspace_size(shapes, inst_image, max_lambdas: int, device: int = 0) -> int:
+    """Device bytes a batch of this shape needs (no GPU needed)."""
+    d, keep = _desc(shapes, inst_image, max_lambdas, device)
+    n = ctypes.c_size_t(0)
+    _check(lib().pmf_workspace_size(ctypes.byref(d), ctypes.byref(n)), "pmf_workspace_size")
+    return int(n.value)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+class Batch:
+    """One batch of grid instances sharing a device workspace."""
+
+    def __init__(self, shapes, inst_image, max_lambdas: int, device: int = 0, stream=None,
+                 workspace=None):
+        import torch
+        self.shapes = [(int(h), int(w)) for h, w in shapes]
+        self.inst_image = [int(i) for i in inst_image]
+        self.max_lambdas = int(max_lambdas)
+        self.device = int(device)
+        d, self._keep = _desc(self.shapes, self.inst_image, self.max_lambdas, self.device)
+        n = ctypes.c_size_t(0)
+        _check(lib().pmf_workspace_size(ctypes.byref(d), ctypes.byref(n)), "pmf_workspace_size")
+        self.workspace_bytes = int(n.value)
+        if workspace is None:
+            workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=f"cuda:{self.device}")
+        self.workspace = workspace
+        self.stream = stream
+        h = ctypes.c_void_p(0)
+        _check(lib().pmf_create_batch(ctypes.byref(d), ctypes.c_void_p(workspace.data_ptr()),
+                                      self.workspace_bytes, _stream_ptr(stream), ctypes.byref(h)),
+               "pmf_create_batch")
+        self._h = h
+        self.n_lambda = 0
+
+    # -- set-up ------------------------------------------------------------------
+    @staticmethod
+    def _arg(a):
+        """(pointer, on_device, keep-alive) for a numpy array or a torch tensor."""
+        try:
+            import torch
+            if isinstance(a, torch.Tensor):
+                if a.dtype != torch.int32:
+                    a = a.to(torch.int32)
+                a = a.contiguous()
+                if a.is_cuda:
+                    return ctypes.c_void_p(a.data_ptr()), 1, a
+                a = a.numpy()
+        except ImportError:
+            pass
+        a = np.ascontiguousarray(a, np.int32)
+        return ctypes.c_void_p(a.ctypes.data), 0, a
+
+    def set_capacities(self, image: int, w_h, w_v):
+        (p1, d1, k1), (p2, d2, k2) = self._arg(w_h), self._arg(w_v)
+        if d1 != d2:
+            raise ValueError("w_h and w_v must both be host or both be device arrays")
+        st = lib().pmf_set_capacities(self._h, int(image), p1, p2, d1)
+        self._pin = (k1, k2)
+        _check(st, "pmf_set_capacities")
+
+    def set_terminals(self, inst: int, src0, slope, sink):
+        args = [self._arg(a) for a in (src0, slope, sink)]
+        if len({a[1] for a in args}) != 1:
+            raise ValueError("src0, slope and sink must all be host or all be device arrays")
+        st = lib().pmf_set_terminals(self._h, int(inst), args[0][0], args[1][0], args[2][0], args[0][1])
+        self._pin2 = [a[2] for a in args]
+        _check(st, "pmf_set_terminals")
+
+    def set_tuning(self, **kw):
+        t = Tuning()
+        _check(lib().pmf_get_tuning(self._h, ctypes.byref(t)), "pmf_get_tuning")
+        for k, v in kw.items():
+            if not hasattr(t, k):
+                raise KeyError(k)
+            setattr(t, k, int(v))
+        _check(lib().pmf_set_tuning(self._h, ctypes.byref(t)), "pmf_set_tuning")
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().pmf_get_tuning(self._h, ctypes.byref(t)), "pmf_get_tuning")
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
+    # -- solve -------------------------------------------------------------------
+    def solve(self, lambdas, stream=None):
+        lam = np.ascontiguousarray(lambdas, np.int32)
+        if lam.ndim == 1:
+            lam = np.broadcast_to(lam, (len(self.inst_image), lam.shape[0])).copy()
+        self.n_lambda = int(lam.shape[1])
+        self._lam = lam
+        st = lib().pmf_solve_schedule(self._h, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      self.n_lambda, _stream_ptr(stream if stream is not None else self.stream))
+        _check(st, "pmf_solve_schedule")
+
+    def sync(self, check: bool = True):
+        per = (ctypes.c_int * len(self.inst_image))()
+        st = lib().pmf_sync(self._h, per)
+        if check:
+            _check(st, "pmf_sync")
+        return [int(x) for x in per]
+
+    # -- results -----------------------------------------------------------------
+    def get_flow(self, inst: int, k: int) -> int:
+        f = ctypes.c_int64(0)
+        _check(lib().pmf_get_flow(self._h, int(inst), int(k), ctypes.byref(f)), "pmf_get_flow")
+        return int(f.value)
+
+    def get_cut(self, inst: int, k: int, out=None):
+        H, W = self.shapes[self.inst_image[inst]]
+        if out is None:
+            out = np.empty((H, W), np.uint8)
+        try:
+            import torch
+            if isinstance(out, torch.Tensor):
+                assert out.is_cuda and out.dtype == torch.uint8 and out.is_contiguous() and out.numel() == H * W
+                _check(lib().pmf_get_cut(self._h, int(inst), int(k), ctypes.c_void_p(out.data_ptr()), 1),
+                       "pmf_get_cut")
+                return out
+        except ImportError:
+            pass
+        assert out.dtype == np.uint8 and out.flags.c_contiguous and out.size == H * W
+        _check(lib().pmf_get_cut(self._h, int(inst), int(k), ctypes.c_void_p(out.ctypes.data), 0),
+               "pmf_get_cut")
+        return out
+
+    def flows(self, inst: int) -> np.ndarray:
+        return np.array([self.get_flow(inst, k) for k in range(self.n_lambda)], np.int64)
+
+    def cuts(self, inst: int) -> np.ndarray:
+        H, W = self.shapes[self.inst_image[inst]]
+        out = np.empty((self.n_lambda, H, W), np.uint8)
+        for k in range(self.n_lambda):
+            self.get_cut(inst, k, out[k])
+        return out
+
+    def stats(self, inst: int) -> dict:
+        s = Stats()
+        _check(lib().pmf_get_stats(self._h, int(inst), ctypes.byref(s)), "pmf_get_stats")
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().pmf_destroy_batch(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_from_workload(wl, device: int = 0, stream=None, device_inputs: bool = False,
+                        **tuning) -> Batch:
+    """A Batch holding every image and instance of an inputs.Workload, with all
+    capacities uploaded (host path, or device path if device_inputs)."""
+    import torch
+    max_l = max(len(i.lambdas) for i in wl.instances)
+    b = Batch([(im.H, im.W) for im in wl.images], [i.image for i in wl.instances], max_l,
+              device=device, stream=stream)
+    if tuning:
+        b.set_tuning(**tuning)
+    conv = (lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).to(f"cuda:{device}")) \
+        if device_inputs else (lambda a: a)
+    for i, im in enumerate(wl.images):
+        b.set_capacities(i, conv(im.w_h), conv(im.w_v))
+    for i, inst in enumerate(wl.instances):
+        b.set_terminals(i, conv(inst.src0), conv(inst.slope), conv(inst.sink))
+    return b
+
+
+def solve_workload(wl, device: int = 0, check: bool = True, **tuning):
+    """Solve every instance of a Workload in one batch.  All instances must have
+    schedules of the same length.  Returns (per-instance statuses, list of
+    (flows [m], masks [m, H, W]))."""
+    lens = {len(i.lambdas) for i in wl.instances}
+    if len(lens) != 1:
+        raise ValueError("solve_workload needs schedules of one length")
+    b = batch_from_workload(wl, device=device, **tuning)
+    b.solve(np.stack([i.lambdas for i in wl.instances]))
+    st = b.sync(check=check)
+    res = []
+    for i in range(len(wl.instances)):
+        if st[i] == PMF_OK:
+            res.append((b.flows(i), b.cuts(i)))
+        else:
+            res.append((None, None))
+    b.close()
+    return st, res

@@ -1,0 +1,71 @@
+"""CUDA path vs the CPU oracle, element by element (flows int64, masks uint8),
+through the C ABI.  Both outputs are unique (the maximum flow value and the
+maximal source set), so the comparison is exact."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1509_06004_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pmf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_06004_b300 import build, pmf as P
+    build.build()
+    return P
+
+
+def check_workload(P, wl, oracle_res=None, **tuning):
+    st, res = P.solve_workload(wl, **tuning)
+    assert all(s == P.PMF_OK for s in st), st
+    if oracle_res is None:
+        oracle_res = oracle.solve_workload(wl)
+    for i, ((gf, gm), (of, om)) in enumerate(zip(res, oracle_res)):
+        assert np.array_equal(gf, of), (i, gf, of)
+        assert np.array_equal(gm, om), (i, np.argwhere(gm != om)[:10])
+    return res
+
+
+def test_single_64x64(pmf):
+    check_workload(pmf, inputs.single_maxflow_64())
+
+
+SHAPES = [(1, 1), (1, 7), (7, 1), (3, 5), (8, 32), (9, 33), (16, 31), (17, 65), (40, 70), (33, 97)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("tile_h", [4, 8])
+def test_random_small_grids(pmf, shape, tile_h):
+    H, W = shape
+    rng = np.random.default_rng(H * 1000 + W)
+    wl = inputs.random_grid(H, W, rng, wmax=20, tmax=40, p_zero=0.2, n_lambda=4, lam_max=30)
+    check_workload(pmf, wl, tile_h=tile_h)
+
+
+@pytest.mark.parametrize("mode", ["persistent", "persistent-nograph", "rounds"])
+def test_modes_on_synthetic_image(pmf, mode):
+    rng = np.random.default_rng(3)
+    img = inputs.make_image(70, 90, 4, 0.05, rng)
+    w_h, w_v = inputs.pairwise_caps(img)
+    wl = inputs.Workload("t")
+    wl.images.append(inputs.Image(70, 90, w_h, w_v, img))
+    lam = inputs.lambda_schedule(8, 10, 5000)
+    for _ in range(3):
+        y0, x0 = inputs.random_seed_origin(70, 90, rng)
+        src0, slope, sink = inputs.terminals(img, inputs.seed_square(70, 90, y0, x0))
+        wl.instances.append(inputs.Instance(0, src0, slope, sink, lam, (y0, x0)))
+    kw = {"persistent": {}, "persistent-nograph": {"use_graph": 0}, "rounds": {"mode": 1}}[mode]
+    check_workload(pmf, wl, **kw)
+
+
+def test_parametric_320x240(pmf):
+    wl = inputs.parametric_320x240()
+    res = check_workload(pmf, wl)
+    flows, masks = res[0]
+    for k in range(len(flows) - 1):
+        assert np.all(masks[k] <= masks[k + 1])
