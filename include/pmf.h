@@ -101,8 +101,24 @@ typedef struct {
     int32_t blocks_per_sm;   /* persistent grid = blocks_per_sm * SMs; default: occupancy */
     int32_t use_graph;       /* 1 = replay the solve as a captured CUDA graph (default 1;
                                 ignored in mode 1) */
-    int32_t reserved;
+    int32_t trace;           /* 1 = record instance phase changes (pmf_get_trace) */
+    int32_t poll_ns;         /* longest sleep of an idle worker warp between polls of
+                                its queue slot, ns; default 256 */
+    int32_t reserved[3];
 } pmf_tuning;
+
+/* One instance phase change recorded on the device (tuning.trace = 1). */
+typedef struct {
+    uint64_t t_ns;           /* device %globaltimer, ns */
+    int32_t inst;
+    int32_t event;           /* 0 global relabel started, 1 lambda step certified,
+                                2 push/relabel restarted after a relabel,
+                                3 instance finished, 4 watchdog stopped it */
+    int32_t k;               /* schedule index after the change */
+    int32_t epoch;           /* global relabel count */
+    int64_t pr_visits;       /* cumulative push/relabel tile visits */
+    int64_t bfs_visits;      /* cumulative relabel tile visits */
+} pmf_trace_event;
 
 /* Per-instance counters of the last solve (pmf_get_stats). */
 typedef struct {
@@ -165,6 +181,31 @@ PMF_API pmf_status pmf_get_cut(pmf_batch *b, int32_t inst, int32_t k, uint8_t *m
  * cost), after pmf_sync. */
 PMF_API pmf_status pmf_get_flow(pmf_batch *b, int32_t inst, int32_t k, int64_t *flow);
 
+/* Every mask of instance inst: n_lambda * H * W bytes, [k][y][x], one copy per
+ * lambda and a single synchronisation (on_device as for pmf_get_cut). */
+PMF_API pmf_status pmf_get_cuts(pmf_batch *b, int32_t inst, uint8_t *masks, int on_device);
+
+/* Every flow value of instance inst: n_lambda int64 (host pointer). */
+PMF_API pmf_status pmf_get_flows(pmf_batch *b, int32_t inst, int64_t *flows);
+
+/* Device time of the last solve, from CUDA events the library records on the
+ * launching stream (pmf_sync first): solve_ms from the start of the reset
+ * kernel to the end of the result copies, worker_ms the persistent worker
+ * kernel alone (summed over rounds in mode 1). */
+PMF_API pmf_status pmf_get_timing(pmf_batch *b, float *solve_ms, float *worker_ms);
+
+/* Phase-change trace of the last solve (tuning.trace = 1), after pmf_sync:
+ * copies up to cap records to out (host) and sets *n to the number recorded
+ * (at most 65536; later events are dropped). */
+PMF_API pmf_status pmf_get_trace(pmf_batch *b, pmf_trace_event *out, int32_t cap, int32_t *n);
+
+/* Warp-time breakdown of the last solve (tuning.trace = 1), after pmf_sync:
+ * out8[0..3] = ns summed over worker warps spent waiting for work, in
+ * push/relabel visits, in global-relabel visits and retiring items; out8[4] =
+ * push/relabel sweeps run; out8[5..7] = SM cycles (summed over visits) of the
+ * push/relabel visits' load, sweep and write-back stages. */
+PMF_API pmf_status pmf_get_profile(pmf_batch *b, uint64_t *out8);
+
 /* Counters of the last solve for one instance, after pmf_sync. */
 PMF_API pmf_status pmf_get_stats(pmf_batch *b, int32_t inst, pmf_stats *out);
 
@@ -177,6 +218,10 @@ PMF_API pmf_status pmf_get_mask_layout(pmf_batch *b, int32_t inst, const uint8_t
 PMF_API void pmf_destroy_batch(pmf_batch *b);
 
 PMF_API const char *pmf_status_string(pmf_status s);
+
+/* Text of the last CUDA failure seen by this thread ("" if none): the call
+ * site and cudaGetErrorString, for diagnostics after PMF_ERR_CUDA. */
+PMF_API const char *pmf_last_error(void);
 
 /* Library version, e.g. "pmf 0.1.0 sm_103a". */
 PMF_API const char *pmf_version(void);

@@ -26,7 +26,7 @@ int round_up_i(int v, int a) { return (v + a - 1) / a * a; }
 
 struct Layout {
     size_t img_planes, inst_planes, masks, dev_inst, ist, tiles, tile_inst, ring, lambdas, flows,
-        globals, staging, img_flags, inst_flags, total;
+        globals, staging, img_flags, inst_flags, trace, total;
     size_t ring_cap;
     size_t max_tiles;
     size_t max_hw;
@@ -70,10 +70,11 @@ Layout make_layout(const pmf_batch_desc *d) {
         inst_elems += (size_t)N_INST_PLANES * ps;
         L.mask_off[i] = (int64_t)mask_bytes;
         mask_bytes += (size_t)d->max_lambdas * ps;
-        L.max_tiles += (size_t)(L.rows[im] / 4) * (L.pitch[im] / TILE_W);   // smallest tile height
+        L.max_tiles += (size_t)(L.rows[im] / 4) * ((d->img_w[im] + TILE_IN - 1) / TILE_IN);   // smallest tile height
     }
+    // every tile can be queued once, and every resident warp may hold a ticket
     L.ring_cap = 1;
-    while (L.ring_cap < L.max_tiles) L.ring_cap <<= 1;
+    while (L.ring_cap < L.max_tiles + 16384) L.ring_cap <<= 1;
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes); return o; };
     L.img_planes = take(img_elems * 4);
@@ -90,6 +91,7 @@ Layout make_layout(const pmf_batch_desc *d) {
     L.staging = take(sizeof(int32_t) * 3 * L.max_hw);
     L.img_flags = take(sizeof(int32_t) * d->n_images);
     L.inst_flags = take(sizeof(int32_t) * d->n_inst);
+    L.trace = take(sizeof(TraceEvent) * TRACE_CAP);
     L.total = off;
     return L;
 }
@@ -120,6 +122,8 @@ struct pmf_batch {
     cudaStream_t setup_stream = nullptr;   // caller's stream for set-up copies
     cudaStream_t cap_stream = nullptr;     // private stream used for graph capture
     cudaEvent_t done = nullptr;
+    cudaEvent_t ev_t0 = nullptr, ev_w0 = nullptr, ev_w1 = nullptr, ev_t1 = nullptr;   // timing
+    float worker_ms_rounds = 0.f;
     bool in_flight = false;
     bool solved = false;
     int32_t last_n_lambda = 0;
@@ -132,14 +136,20 @@ struct pmf_batch {
     DevInst *dinst_h = nullptr;
     // captured graph
     cudaGraphExec_t gexec = nullptr;
-    int graph_n_lambda = -1;
-    int graph_key = -1;
+    bool graph_valid = false;
     int worker_grid = 0;
 };
 
 namespace {
 
-pmf_status cuda_err(cudaError_t e) { return e == cudaSuccess ? PMF_OK : PMF_ERR_CUDA; }
+thread_local char g_last_error[256] = "";
+
+pmf_status cuda_err_at(cudaError_t e, const char *where) {
+    if (e == cudaSuccess) return PMF_OK;
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
+    return PMF_ERR_CUDA;
+}
+#define cuda_err(e) cuda_err_at((e), __func__)
 
 void apply_defaults(pmf_tuning *t) {
     if (t->tile_h != 4 && t->tile_h != 8) t->tile_h = 8;
@@ -148,6 +158,8 @@ void apply_defaults(pmf_tuning *t) {
     if (t->max_visits_per_tile <= 0) t->max_visits_per_tile = 2000;
     if (t->mode != 1) t->mode = 0;
     if (t->use_graph != 0) t->use_graph = 1;
+    t->trace = t->trace ? 1 : 0;
+    if (t->poll_ns <= 0) t->poll_ns = 256;
 }
 
 // per-instance tile geometry for the current tile height; uploads the table
@@ -162,7 +174,7 @@ pmf_status refresh_geometry(pmf_batch *b, cudaStream_t s) {
         d.rows = b->L.rows[im];
         d.pitch = b->L.pitch[im];
         d.image = im;
-        d.tiles_x = d.pitch / TILE_W;
+        d.tiles_x = (d.W + TILE_IN - 1) / TILE_IN;
         d.tiles_y = d.rows / th;
         d.n_tiles = d.tiles_x * d.tiles_y;
         d.tile_base = base;
@@ -188,14 +200,21 @@ int grid_size(pmf_batch *b) {
 }
 
 // the launch sequence of one solve (persistent mode)
-pmf_status enqueue_solve(pmf_batch *b, int n_lambda, cudaStream_t s) {
+pmf_status enqueue_solve(pmf_batch *b, int n_lambda, cudaStream_t s, bool capturing) {
+    // inside a stream capture the timing events become event-record nodes
+    auto rec = [&](cudaEvent_t ev) {
+        return capturing ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal) : cudaEventRecord(ev, s);
+    };
     const size_t lam_bytes = sizeof(int32_t) * (size_t)b->desc.n_inst * b->desc.max_lambdas;
     cudaError_t e = cudaMemcpyAsync(b->ws + b->L.lambdas, b->lam_h, lam_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = rec(b->ev_t0);
     if (e == cudaSuccess) e = launch_reset(b->P, s);
     int maxpix = 0;
     for (int i = 0; i < b->desc.n_inst; ++i) maxpix = std::max(maxpix, b->dinst[i].rows * b->dinst[i].pitch);
     if (e == cudaSuccess) e = launch_init(b->P, maxpix, s);
+    if (e == cudaSuccess) e = rec(b->ev_w0);
     if (e == cudaSuccess) e = launch_worker(b->P, b->worker_grid, s);
+    if (e == cudaSuccess) e = rec(b->ev_w1);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->ist_h, b->ws + b->L.ist, sizeof(InstState) * b->desc.n_inst, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)
@@ -203,6 +222,7 @@ pmf_status enqueue_solve(pmf_batch *b, int n_lambda, cudaStream_t s) {
                             cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->glob_h, b->ws + b->L.globals, sizeof(Globals), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = rec(b->ev_t1);
     (void)n_lambda;
     return cuda_err(e);
 }
@@ -212,6 +232,8 @@ pmf_status enqueue_solve(pmf_batch *b, int n_lambda, cudaStream_t s) {
 extern "C" {
 
 const char *pmf_version(void) { return "pmf 0.1.0 sm_103a"; }
+
+const char *pmf_last_error(void) { return g_last_error; }
 
 const char *pmf_status_string(pmf_status s) {
     switch (s) {
@@ -266,6 +288,10 @@ pmf_status pmf_create_batch(const pmf_batch_desc *desc, void *dev_workspace, siz
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->dinst_h, sizeof(DevInst) * desc->n_inst, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev_t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev_w0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev_w1);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev_t1);
     if (e != cudaSuccess) {
         pmf_destroy_batch(b);
         return PMF_ERR_CUDA;
@@ -325,7 +351,7 @@ pmf_status pmf_set_tuning(pmf_batch *b, const pmf_tuning *t) {
     pmf_tuning n = *t;
     apply_defaults(&n);
     b->tune = n;
-    b->graph_key = -1;   // re-capture on next solve
+    b->graph_valid = false;   // re-capture on next solve
     return PMF_OK;
 }
 
@@ -417,7 +443,9 @@ pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_la
         for (int k = 0; k < b->desc.max_lambdas; ++k)
             b->lam_h[(size_t)i * b->desc.max_lambdas + k] =
                 lambdas[(size_t)i * n_lambda + std::min(k, n_lambda - 1)];
+    b->P.trace = b->tune.trace ? (TraceEvent *)(b->ws + b->L.trace) : nullptr;
     b->P.sweeps = b->tune.sweeps;
+    b->P.poll_ns = b->tune.poll_ns;
     b->P.relabel_pct = b->tune.relabel_every;
     b->P.max_visits_per_tile = b->tune.max_visits_per_tile;
     const bool geo_changed = (b->P.tile_h != b->tune.tile_h) || (b->last_n_lambda != n_lambda);
@@ -427,16 +455,18 @@ pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_la
         const pmf_status st = refresh_geometry(b, s);
         if (st != PMF_OK) return st;
         b->last_n_lambda = n_lambda;
-        b->graph_key = -1;
+        b->graph_valid = false;
     }
     b->worker_grid = grid_size(b);
     b->solved = false;
     cudaError_t e = cudaSuccess;
     if (b->tune.mode == 1) {
         // host-polled rounds: one worker launch per round, the host reads the
-        // number of pending items after each (the one-call-per-iteration form)
+        // number of finished instances after each (the one-call-per-iteration form)
         const size_t lam_bytes = sizeof(int32_t) * (size_t)b->desc.n_inst * b->desc.max_lambdas;
         e = cudaMemcpyAsync(b->ws + b->L.lambdas, b->lam_h, lam_bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_t0, s);
+        b->worker_ms_rounds = 0.f;
         if (e == cudaSuccess) e = launch_reset(b->P, s);
         int maxpix = 0;
         for (int i = 0; i < b->desc.n_inst; ++i) maxpix = std::max(maxpix, b->dinst[i].rows * b->dinst[i].pitch);
@@ -446,10 +476,14 @@ pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_la
             const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
             if (el * 1e9 > (double)b->P.max_ns) break;
             e = launch_begin_round(b->P, s);
+            if (e == cudaSuccess) e = cudaEventRecord(b->ev_w0, s);
             if (e == cudaSuccess) e = launch_worker(b->P, b->worker_grid, s);
+            if (e == cudaSuccess) e = cudaEventRecord(b->ev_w1, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(b->glob_h, b->ws + b->L.globals, sizeof(Globals), cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess || b->glob_h->pending <= 0 || b->glob_h->err) break;
+            float ms = 0.f;
+            if (e == cudaSuccess && cudaEventElapsedTime(&ms, b->ev_w0, b->ev_w1) == cudaSuccess) b->worker_ms_rounds += ms;
+            if (e != cudaSuccess || b->glob_h->inst_done >= b->desc.n_inst || b->glob_h->err) break;
         }
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(b->ist_h, b->ws + b->L.ist, sizeof(InstState) * b->desc.n_inst, cudaMemcpyDeviceToHost, s);
@@ -458,29 +492,31 @@ pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_la
                                 cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(b->glob_h, b->ws + b->L.globals, sizeof(Globals), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_t1, s);
     } else if (b->tune.use_graph) {
-        const int key = b->tune.tile_h * 1000003 + n_lambda * 131 + b->worker_grid;
-        if (b->graph_key != key || !b->gexec) {
+        // the kernel parameters are baked into the graph: set_tuning and a
+        // geometry change invalidate it (graph_valid = false)
+        if (!b->graph_valid || !b->gexec) {
             if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
             cudaGraph_t graph = nullptr;
             e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                const pmf_status st = enqueue_solve(b, n_lambda, b->cap_stream);
+                const pmf_status st = enqueue_solve(b, n_lambda, b->cap_stream, true);
                 const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
                 e = (st != PMF_OK) ? cudaErrorUnknown : e2;
             }
             if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, graph, 0);
             if (graph) cudaGraphDestroy(graph);
-            if (e != cudaSuccess) { b->gexec = nullptr; return PMF_ERR_CUDA; }
-            b->graph_key = key;
+            if (e != cudaSuccess) { b->gexec = nullptr; return cuda_err_at(e, "graph capture"); }
+            b->graph_valid = true;
         }
         e = cudaGraphLaunch(b->gexec, s);
     } else {
-        const pmf_status st = enqueue_solve(b, n_lambda, s);
+        const pmf_status st = enqueue_solve(b, n_lambda, s, false);
         if (st != PMF_OK) return st;
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->done, s);
-    if (e != cudaSuccess) return PMF_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_err_at(e, "solve launch");
     b->in_flight = true;
     return PMF_OK;
 }
@@ -532,6 +568,64 @@ pmf_status pmf_get_flow(pmf_batch *b, int32_t inst, int32_t k, int64_t *flow) {
     return PMF_OK;
 }
 
+pmf_status pmf_get_cuts(pmf_batch *b, int32_t inst, uint8_t *masks, int on_device) {
+    if (!b || !masks || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
+    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
+    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->last_n_lambda) return PMF_ERR_NOT_READY;
+    DeviceGuard dg(b->device);
+    const DevInst &d = b->dinst[inst];
+    const size_t ps = (size_t)d.rows * d.pitch, hw = (size_t)d.H * d.W;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < b->last_n_lambda && e == cudaSuccess; ++k) {
+        const char *src = b->ws + b->L.masks + d.mask_off + (size_t)k * ps;
+        e = cudaMemcpy2DAsync(masks + (size_t)k * hw, d.W, src, d.pitch, d.W, d.H,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->cap_stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap_stream);
+    return cuda_err(e);
+}
+
+pmf_status pmf_get_flows(pmf_batch *b, int32_t inst, int64_t *flows) {
+    if (!b || !flows || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
+    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
+    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->last_n_lambda) return PMF_ERR_NOT_READY;
+    for (int k = 0; k < b->last_n_lambda; ++k) flows[k] = b->flows_h[(size_t)inst * b->desc.max_lambdas + k];
+    return PMF_OK;
+}
+
+pmf_status pmf_get_timing(pmf_batch *b, float *solve_ms, float *worker_ms) {
+    if (!b || !solve_ms || !worker_ms) return PMF_ERR_INVALID_ARG;
+    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
+    DeviceGuard dg(b->device);
+    if (cudaEventElapsedTime(solve_ms, b->ev_t0, b->ev_t1) != cudaSuccess) return PMF_ERR_CUDA;
+    if (b->tune.mode == 1) {
+        *worker_ms = b->worker_ms_rounds;
+    } else if (cudaEventElapsedTime(worker_ms, b->ev_w0, b->ev_w1) != cudaSuccess) {
+        return PMF_ERR_CUDA;
+    }
+    return PMF_OK;
+}
+
+pmf_status pmf_get_trace(pmf_batch *b, pmf_trace_event *out, int32_t cap, int32_t *n) {
+    if (!b || !n || cap < 0 || (cap > 0 && !out)) return PMF_ERR_INVALID_ARG;
+    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
+    static_assert(sizeof(pmf_trace_event) == sizeof(TraceEvent), "trace record layout");
+    const unsigned long long total = b->tune.trace ? b->glob_h->trace_n : 0;
+    const int32_t have = (int32_t)std::min<unsigned long long>(total, (unsigned long long)TRACE_CAP);
+    *n = have;
+    const int32_t m = std::min(have, cap);
+    if (m == 0) return PMF_OK;
+    DeviceGuard dg(b->device);
+    return cuda_err(cudaMemcpy(out, b->ws + b->L.trace, sizeof(TraceEvent) * m, cudaMemcpyDeviceToHost));
+}
+
+pmf_status pmf_get_profile(pmf_batch *b, uint64_t *out8) {
+    if (!b || !out8) return PMF_ERR_INVALID_ARG;
+    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
+    for (int j = 0; j < 8; ++j) out8[j] = b->tune.trace ? b->glob_h->prof[j] : 0;
+    return PMF_OK;
+}
+
 pmf_status pmf_get_stats(pmf_batch *b, int32_t inst, pmf_stats *out) {
     if (!b || !out || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
     if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
@@ -560,6 +654,8 @@ void pmf_destroy_batch(pmf_batch *b) {
     if (b->in_flight && b->done) cudaEventSynchronize(b->done);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->done) cudaEventDestroy(b->done);
+    for (cudaEvent_t ev : {b->ev_t0, b->ev_w0, b->ev_w1, b->ev_t1})
+        if (ev) cudaEventDestroy(ev);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->lam_h) cudaFreeHost(b->lam_h);
     if (b->ist_h) cudaFreeHost(b->ist_h);

@@ -8,7 +8,9 @@
 
 namespace pmf {
 
-constexpr int TILE_W = 32;                 // tile width = one warp, lane = column
+constexpr int TILE_W = 32;                 // row pitch alignment (one warp = 32 lanes)
+constexpr int TILE_IN = 30;                // interior columns of a tile: lanes 1..30; lanes 0
+                                           // and 31 mirror the neighbouring tiles' columns
 constexpr int ROW_ALIGN = 16;              // rows padded so tile heights 4/8/16 divide them
 constexpr int32_t HINF = 0x3fffffff;       // label of a pixel that cannot reach t
 constexpr int N_INST_PLANES = 8;           // e, h, rt, fR, fD, src0, slope, ct
@@ -35,31 +37,55 @@ struct DevInst {                 // read-only during a solve
     int64_t plane_off;           // int32 elements from the instance-plane base
     int64_t img_off;             // int32 elements from the image-plane base
     int64_t mask_off;            // bytes from the mask base
+    int64_t pad2_;               // keeps the size a multiple of 16 bytes
 };
 
 struct InstState {               // mutable during a solve
-    int32_t phase, k, epoch, outstanding;
-    int32_t active, want_bfs, status, vflags;
-    unsigned long long flow;     // int64 two's complement
-    int32_t pr_since, pad_;
-    unsigned long long pr_visits, bfs_visits, epochs, visits_step;
+    // written only by the warp that runs a phase change (nothing of the
+    // instance is queued or running then); read by the workers
+    int32_t phase, k, epoch, status;
+    int32_t vflags, pad0_, pad1_, pad2_;
+    unsigned long long pr_mark;      // pr_visits when the current push/relabel phase began
+    unsigned long long step_mark;    // pr_visits + bfs_visits when the current lambda step began
+    unsigned long long epochs;       // global relabels so far
+    // updated atomically by the workers
+    int32_t outstanding, active, want_bfs, pad3_;
+    unsigned long long flow;         // int64 two's complement: total flow into t
+    unsigned long long pr_visits, bfs_visits;
 };
+
+// trace record of an instance phase change
+struct TraceEvent {
+    unsigned long long t_ns;
+    int32_t inst, event, k, epoch;
+    long long pr_visits, bfs_visits;
+};
+enum TraceKind { TR_BFS_START = 0, TR_STEP_DONE = 1, TR_PR_START = 2, TR_DONE = 3, TR_NOT_CONVERGED = 4 };
+constexpr int TRACE_CAP = 1 << 16;
 
 struct TileState {
     int32_t state, epoch, lam, active;
 };
 
+// the queue counters sit on separate 128-byte lines: head is hit by every pop,
+// tail by every push
 struct Globals {
-    unsigned long long head, tail;
+    alignas(128) unsigned long long head;
+    alignas(128) unsigned long long tail;
+    alignas(128) int32_t inst_done;  // instances that reached PH_DONE (the launch ends at n_inst)
+    alignas(128) int32_t err, round_mode;
     unsigned long long round_end;
-    long long pending;
-    unsigned long long completed;
-    int32_t err, round_mode;
-    unsigned long long items;    // total items processed (stat)
-    unsigned long long t_start;  // %globaltimer at the start of the launch
+    unsigned long long t_start;      // %globaltimer at the start of the launch
+    alignas(128) unsigned long long trace_n;
+    // warp-time breakdown (ns summed over warps), recorded with the trace:
+    // [0] waiting for work, [1] push/relabel visits, [2] relabel (BFS) visits,
+    // [3] retiring items (wake-ups, requeue, phase changes), [4] sweeps run,
+    // [5..7] SM cycles in the load, sweep and write-back stages of push/relabel visits
+    unsigned long long prof[8];
 };
 
 struct Params {
+    TraceEvent *trace;           // phase-change trace (TRACE_CAP records) or nullptr
     int32_t *planes;             // instance planes base
     const int32_t *img;          // image planes base
     uint8_t *masks;
@@ -76,6 +102,7 @@ struct Params {
     unsigned long long ring_mask;
     int32_t n_inst, n_tiles_total, max_lambdas, sweeps;
     int32_t relabel_pct, tile_h;
+    int32_t poll_ns, pad_p_;
     long long max_visits_per_tile;
     long long stall_ns;          // a worker gives up after this long without progress
     long long max_ns;            // ... or after this long in one launch

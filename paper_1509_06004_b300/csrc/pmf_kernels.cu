@@ -56,16 +56,12 @@ __device__ __forceinline__ unsigned long long ldv64(const unsigned long long *p)
 }
 __device__ __forceinline__ long long ldv64s(const long long *p) { return *(const volatile long long *)p; }
 
+// per-warp scratch: values of the two border columns at load (their updates
+// are written back as deltas)
 template <int TH>
 struct WarpSmem {
-    int lh[TH];    // left halo column: label
-    int lw[TH];    //   w_h of the edge (x0-1) - x0
-    int lf[TH];    //   flow on that edge (local copy, changed by lane 0's pushes)
-    int lf0[TH];   //   its value at load
-    int lout[TH];  //   excess pushed into the left halo pixel
-    int rh[TH];    // right halo column: label
-    int rout[TH];  //   excess pushed into the right halo pixel
-    int rf0[TH];   //   lane 31's own fR at load (the right border edge)
+    int e0[2][TH];   // excess of lanes 1 and 30 at load
+    int f0[2][TH];   // fR of lane 0 (left border edge) and lane 30 (right border edge)
 };
 
 // --------------------------------------------------------------------------
@@ -98,67 +94,79 @@ __device__ void push1(const Params &P, int v) {   // one lane
     *slot = v;
 }
 
-__device__ int ring_pop(const Params &P) {   // one lane; -1 = stop
+// persistent mode: every pop takes a ticket with one atomicAdd and then waits
+// on its own ring slot, so idle warps poll distinct addresses.  The ring has
+// room for every tile plus every resident warp's ticket, so a slot is never
+// shared by two outstanding tickets.
+__device__ int ring_pop_ticket(const Params &P) {   // one lane; -1 = stop
     Globals *G = P.g;
-    unsigned long long last_c = ~0ULL, t_since = 0;
-    unsigned ns = 64;
-    for (;;) {
-        if (ldv(&G->err)) return -1;
-        if (gtime_ns() - ldv64(&G->t_start) > (unsigned long long)P.max_ns) {
-            atomicOr(&G->err, GE_TIMEOUT);
-            return -1;
+    const unsigned long long h = atomicAdd(&G->head, 1ULL);
+    volatile int *slot = (volatile int *)(P.ring + (h & P.ring_mask));
+    unsigned ns = 32;
+    unsigned long long last_tail = ~0ULL, t_since = 0;
+    int last_pend = -1;
+    for (unsigned polls = 1;; ++polls) {
+        const int v = *slot;
+        if (v != -1) {
+            *slot = -1;
+            __threadfence();
+            return v;
         }
-        unsigned long long h = ldv64(&G->head);
-        unsigned long long t = ldv64(&G->tail);
-        unsigned long long lim = t;
-        if (G->round_mode) {
-            unsigned long long re = ldv64(&G->round_end);
-            if (h >= re) return -1;
-            if (re < lim) lim = re;
-        }
-        if (h < lim) {
-            if (atomicCAS(&G->head, h, h + 1) == h) {
-                volatile int *slot = (volatile int *)(P.ring + (h & P.ring_mask));
-                int v;
-                if (!slot_wait(P, slot, false, &v)) return -1;
-                *slot = -1;
-                __threadfence();
-                return v;
+        if ((polls & 3) == 0) {
+            if (ldv(&G->err)) return -1;
+            const int ndone = ldv(&G->inst_done);
+            if (ndone >= P.n_inst) return -1;
+            const unsigned long long now = gtime_ns();
+            if (now - ldv64(&G->t_start) > (unsigned long long)P.max_ns) {
+                atomicOr(&G->err, GE_TIMEOUT);
+                return -1;
             }
-            continue;
-        }
-        if (ldv64s(&G->pending) <= 0) return -1;
-        unsigned long long c = ldv64(&G->completed);
-        unsigned long long now = gtime_ns();
-        if (c != last_c) { last_c = c; t_since = now; }
-        else if (now - t_since > (unsigned long long)P.stall_ns) {
-            atomicOr(&G->err, GE_STALL);
-            return -1;
+            const unsigned long long tl = ldv64(&G->tail);
+            if (tl != last_tail || ndone != last_pend) {
+                last_tail = tl;
+                last_pend = ndone;
+                t_since = now;
+            } else if (now - t_since > (unsigned long long)P.stall_ns) {
+                atomicOr(&G->err, GE_STALL);
+                return -1;
+            }
         }
         __nanosleep(ns);
-        if (ns < 8192) ns <<= 1;
+        if (ns < (unsigned)P.poll_ns) ns <<= 1;
     }
 }
 
-// ask for tile t (same instance) to be visited; one lane
-__device__ void request(const Params &P, int t, int inst) {
-    int *st = &P.tiles[t].state;
-    for (int it = 0; it < 1024; ++it) {
-        int old = atomicCAS(st, T_IDLE, T_QUEUED);
-        if (old == T_IDLE) {
-            atomicAdd(&P.ist[inst].outstanding, 1);
-            atomicAdd((unsigned long long *)&P.g->pending, 1ULL);
+// round mode (host-polled): claim only tickets below the round's end
+__device__ int ring_pop_round(const Params &P) {   // one lane; -1 = round over
+    Globals *G = P.g;
+    for (int it = 0; it < (1 << 20); ++it) {
+        if (ldv(&G->err)) return -1;
+        const unsigned long long h = ldv64(&G->head);
+        const unsigned long long re = ldv64(&G->round_end);
+        if (h >= re) return -1;
+        if (atomicCAS(&G->head, h, h + 1) == h) {
+            volatile int *slot = (volatile int *)(P.ring + (h & P.ring_mask));
+            int v;
+            if (!slot_wait(P, slot, false, &v)) return -1;
+            *slot = -1;
             __threadfence();
-            push1(P, t);
-            return;
+            return v;
         }
-        if (old == T_QUEUED || old == T_DIRTY) return;
-        // RUNNING: mark dirty so that its visitor runs it again
-        int o2 = atomicCAS(st, T_RUNNING, T_DIRTY);
-        if (o2 == T_RUNNING || o2 == T_DIRTY || o2 == T_QUEUED) return;
-        // it went IDLE in between: retry
     }
-    atomicOr(&P.g->err, GE_RING);
+    atomicOr(&G->err, GE_RING);
+    return -1;
+}
+
+// read-only instance descriptor through the non-coherent (texture) path; the
+// table is written before the worker launch and never during it
+__device__ __forceinline__ DevInst load_inst(const Params &P, int inst) {
+    static_assert(sizeof(DevInst) % 16 == 0, "DevInst is loaded as int4s");
+    DevInst d;
+    const int4 *src = reinterpret_cast<const int4 *>(P.inst + inst);
+    int4 *dst = reinterpret_cast<int4 *>(&d);
+#pragma unroll
+    for (int j = 0; j < (int)(sizeof(DevInst) / 16); ++j) dst[j] = __ldg(src + j);
+    return d;
 }
 
 // --------------------------------------------------------------------------
@@ -178,12 +186,11 @@ __device__ void enqueue_tiles(const Params &P, int inst, const DevInst &D, bool 
         unsigned long long base = 0;
         if (lane == 0) {
             atomicAdd(&P.ist[inst].outstanding, cnt);
-            atomicAdd((unsigned long long *)&P.g->pending, (unsigned long long)cnt);
             __threadfence();
             base = atomicAdd(&P.g->tail, (unsigned long long)cnt);
         }
         base = __shfl_sync(FULL_MASK, base, 0);
-        __threadfence();
+        __syncwarp();
         if (sel) {
             const unsigned long long tk = base + __popc(m & ((1u << lane) - 1u));
             volatile int *slot = (volatile int *)(P.ring + (tk & P.ring_mask));
@@ -193,45 +200,68 @@ __device__ void enqueue_tiles(const Params &P, int inst, const DevInst &D, bool 
     }
 }
 
+__device__ void trace(const Params &P, int inst, int event, volatile InstState *S) {
+    if (!P.trace) return;
+    const unsigned long long i = atomicAdd(&P.g->trace_n, 1ULL);
+    if (i >= (unsigned long long)TRACE_CAP) return;
+    TraceEvent e;
+    e.t_ns = gtime_ns();
+    e.inst = inst;
+    e.event = event;
+    e.k = S->k;
+    e.epoch = S->epoch;
+    e.pr_visits = (long long)S->pr_visits;
+    e.bfs_visits = (long long)S->bfs_visits;
+    P.trace[i] = e;
+}
+
 __device__ void transition(const Params &P, int inst) {
     const int lane = threadIdx.x & 31;
     volatile InstState *S = P.ist + inst;
-    const DevInst D = P.inst[inst];
+    const DevInst D = load_inst(P, inst);
     __threadfence();
     int mode = 0;   // 0 nothing, 1 all tiles, 2 tiles with active pixels
     if (lane == 0) {
         const int phase = S->phase;
         if (S->status != PMF_OK) {
             S->phase = PH_DONE;
+            atomicAdd(&P.g->inst_done, 1);
         } else if (phase == PH_PR) {           // start a global relabel
             S->epoch = S->epoch + 1;
             S->epochs = S->epochs + 1;
             S->phase = PH_BFS;
             S->want_bfs = 0;
-            S->pr_since = 0;
             mode = 1;
+            trace(P, inst, TR_BFS_START, S);
         } else if (phase == PH_BFS) {
+            const unsigned long long visits = S->pr_visits + S->bfs_visits;
             if (S->active == 0) {              // lambda step certified: record, advance
                 const int k = S->k;
                 P.flows[(size_t)inst * P.max_lambdas + k] = (long long)S->flow;
                 S->k = k + 1;
-                S->visits_step = 0;
+                S->step_mark = visits;
+                trace(P, inst, TR_STEP_DONE, S);
                 if (k + 1 >= D.n_lambda) {
                     S->phase = PH_DONE;
+                    atomicAdd(&P.g->inst_done, 1);
+                    trace(P, inst, TR_DONE, S);
                 } else {
                     S->phase = PH_PR;
-                    S->pr_since = 0;
+                    S->pr_mark = S->pr_visits;
                     S->want_bfs = 0;
                     mode = 1;
                 }
-            } else if ((long long)S->visits_step > P.max_visits_per_tile * (long long)D.n_tiles) {
+            } else if ((long long)(visits - S->step_mark) > P.max_visits_per_tile * (long long)D.n_tiles) {
                 S->status = PMF_ERR_NOT_CONVERGED;
                 S->phase = PH_DONE;
+                atomicAdd(&P.g->inst_done, 1);
+                trace(P, inst, TR_NOT_CONVERGED, S);
             } else {
                 S->phase = PH_PR;
-                S->pr_since = 0;
+                S->pr_mark = S->pr_visits;
                 S->want_bfs = 0;
                 mode = 2;
+                trace(P, inst, TR_PR_START, S);
             }
         }
         __threadfence();
@@ -241,50 +271,106 @@ __device__ void transition(const Params &P, int inst) {
 }
 
 // finish an item: wake neighbours, requeue or retire the tile, maybe change
-// the instance's phase
+// the instance's phase.  Lanes 0-3 wake the four neighbours in parallel, lane 4
+// settles this tile; the instance's outstanding count changes once by the net
+// number of items (pushed - 1), BEFORE the new items become visible.
 __device__ void finish(const Params &P, int g, int inst, int phase, bool requeue, unsigned nb,
                        const DevInst &D) {
     const int lane = threadIdx.x & 31;
-    int trans = 0, again = 0;
-    if (lane == 0) {
-        volatile InstState *IS = P.ist + inst;
-        bool allow = false;
-        if (IS->status == PMF_OK) {
-            if (phase == PH_BFS) allow = true;
-            else if (phase == PH_PR) allow = (IS->want_bfs == 0);
+    volatile InstState *IS = P.ist + inst;
+    bool allow = false;
+    if (IS->status == PMF_OK) {
+        if (phase == PH_BFS) allow = true;
+        else if (phase == PH_PR) allow = (IS->want_bfs == 0);
+    }
+    int item = -1;
+    if (allow && lane < 4 && ((nb >> lane) & 1u)) {
+        const int lt = g - D.tile_base;
+        const int ty = lt / D.tiles_x, tx = lt - ty * D.tiles_x;
+        int t = -1;
+        if (lane == 0 && ty > 0) t = g - D.tiles_x;
+        if (lane == 1 && ty < D.tiles_y - 1) t = g + D.tiles_x;
+        if (lane == 2 && tx > 0) t = g - 1;
+        if (lane == 3 && tx < D.tiles_x - 1) t = g + 1;
+        if (t >= 0) {
+            int *st = &P.tiles[t].state;
+            for (int it = 0; it < 1024; ++it) {
+                const int old = atomicCAS(st, T_IDLE, T_QUEUED);
+                if (old == T_IDLE) { item = t; break; }
+                if (old == T_QUEUED || old == T_DIRTY) break;
+                const int o2 = atomicCAS(st, T_RUNNING, T_DIRTY);   // its visitor will run it again
+                if (o2 != T_IDLE) break;
+                if (it == 1023) atomicOr(&P.g->err, GE_RING);
+            }
         }
-        if (allow && nb) {
-            const int lt = g - D.tile_base;
-            const int ty = lt / D.tiles_x, tx = lt - ty * D.tiles_x;
-            if ((nb & 1) && ty > 0) request(P, g - D.tiles_x, inst);
-            if ((nb & 2) && ty < D.tiles_y - 1) request(P, g + D.tiles_x, inst);
-            if ((nb & 4) && tx > 0) request(P, g - 1, inst);
-            if ((nb & 8) && tx < D.tiles_x - 1) request(P, g + 1, inst);
-        }
+    }
+    if (lane == 4) {
         int *st = &P.tiles[g].state;
         if (requeue && allow) {
             atomicExch(st, T_QUEUED);
-            again = 1;
+            item = g;
         } else {
             const int old = atomicCAS(st, T_RUNNING, T_IDLE);
             if (old == T_DIRTY) {
-                if (allow) { atomicExch(st, T_QUEUED); again = 1; }
+                if (allow) { atomicExch(st, T_QUEUED); item = g; }
                 else atomicExch(st, T_IDLE);
             }
         }
-        if (again) {
-            __threadfence();
-            push1(P, g);
-        } else {
-            const int o = atomicSub(&P.ist[inst].outstanding, 1);
-            trans = (o == 1);
-        }
-        atomicAdd(&P.g->completed, 1ULL);
     }
+    const unsigned pm = __ballot_sync(FULL_MASK, item >= 0);
+    const int k = __popc(pm);
+    int trans = 0;
+    unsigned long long base = 0;
+    if (lane == 0) {
+        const int delta = k - 1;
+        if (delta != 0) {
+            const int old = atomicAdd(&P.ist[inst].outstanding, delta);
+            trans = (old + delta == 0);
+        }
+        if (k) {
+            __threadfence();
+            base = atomicAdd(&P.g->tail, (unsigned long long)k);
+        }
+    }
+    base = __shfl_sync(FULL_MASK, base, 0);
     trans = __shfl_sync(FULL_MASK, trans, 0);
-    again = __shfl_sync(FULL_MASK, again, 0);
+    __syncwarp();
+    if (item >= 0) {
+        const unsigned long long tk = base + __popc(pm & ((1u << lane) - 1u));
+        volatile int *slot = (volatile int *)(P.ring + (tk & P.ring_mask));
+        int dummy;
+        if (slot_wait(P, slot, true, &dummy)) *slot = item;
+    }
     if (trans) transition(P, inst);
-    if (lane == 0 && !again) atomicAdd((unsigned long long *)&P.g->pending, ~0ULL);   // -1
+}
+
+// --------------------------------------------------------------------------
+// push/relabel visit of one tile (Goldberg-Tarjan push and relabel operations,
+// the solver the paper runs through NPPI, Section 3)
+// --------------------------------------------------------------------------
+// Tile geometry.  A tile is TH rows x 30 interior columns.  Lane l of the warp
+// holds column X = 30*tx - 1 + l in registers (TH pixels); lanes 0 and 31 are
+// "ghost" lanes holding the neighbouring tiles' border columns: their labels
+// are read-only for the visit, flow pushed into them accumulates in their
+// registers and is added to the neighbour's state at write-back.  Every lane
+// runs the same straight-line code, so the independent rows of a sweep
+// overlap.
+struct TileGeo {
+    int ty, tx, y0, X, lane;
+    bool ghost, inb;
+};
+
+__device__ __forceinline__ TileGeo tile_geo(int g, const DevInst &D, int TH) {
+    TileGeo t;
+    t.lane = threadIdx.x & 31;
+    const int lt = g - D.tile_base;
+    t.ty = lt / D.tiles_x;
+    t.tx = lt - t.ty * D.tiles_x;
+    t.y0 = t.ty * TH;
+    t.X = t.tx * TILE_IN - 1 + t.lane;
+    t.ghost = (t.lane == 0) || (t.lane == 31);
+    t.inb = (t.X >= 0) && (t.X < D.pitch);
+    return t;
 }
 
 // --------------------------------------------------------------------------
@@ -294,10 +380,9 @@ __device__ void finish(const Params &P, int g, int inst, int phase, bool requeue
 template <int TH>
 __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, const DevInst &D,
                          int kcur, bool &self_active, unsigned &nbmask) {
-    const int lane = threadIdx.x & 31;
-    const int lt = g - D.tile_base;
-    const int ty = lt / D.tiles_x, tx = lt - ty * D.tiles_x;
-    const int x0 = tx * TILE_W, y0 = ty * TH, x = x0 + lane;
+    const TileGeo T = tile_geo(g, D, TH);
+    const int lane = T.lane;
+    const bool own = T.inb && !T.ghost;     // a pixel this tile updates
     const int pitch = D.pitch;
     const size_t PS = (size_t)D.rows * pitch;
     int *base = P.planes + D.plane_off;
@@ -306,23 +391,33 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
     const int *SLOPE = base + P_SLOPE * PS;
     const int *WH = P.img + D.img_off;
     const int *WV = WH + PS;
+    const long long c_start = P.trace ? clock64() : 0;
 
-    int e[TH], h[TH], rt[TH], fr[TH], fd[TH], wh[TH], wv[TH], e0[TH];
+    int e[TH], h[TH], rt[TH], fr[TH], fd[TH], wh[TH], wv[TH];
     long long srt0 = 0;
 #pragma unroll
     for (int i = 0; i < TH; ++i) {
-        const size_t idx = (size_t)(y0 + i) * pitch + x;
-        e[i] = __ldcg(E + idx);
-        h[i] = __ldcg(Hh + idx);
-        rt[i] = __ldcg(RT + idx);
-        fr[i] = __ldcg(FR + idx);
-        fd[i] = __ldcg(FD + idx);
-        wh[i] = __ldg(WH + idx);
-        wv[i] = __ldg(WV + idx);
-        e0[i] = e[i];
+        const size_t idx = (size_t)(T.y0 + i) * pitch + T.X;
+        e[i] = own ? __ldcg(E + idx) : 0;
+        h[i] = T.inb ? __ldcg(Hh + idx) : HINF;
+        rt[i] = own ? __ldcg(RT + idx) : 0;
+        fr[i] = (T.inb && lane != 31) ? __ldcg(FR + idx) : 0;
+        fd[i] = own ? __ldcg(FD + idx) : 0;
+        wh[i] = (T.inb && lane != 31) ? __ldg(WH + idx) : 0;
+        wv[i] = own ? __ldg(WV + idx) : 0;
         srt0 += rt[i];
     }
-    const int fd0b = fd[TH - 1];
+    const int e0top = e[0], e0bot = e[TH - 1], fd0b = fd[TH - 1];
+    if (lane == 1 || lane == 30) {
+        const int c = lane == 1 ? 0 : 1;
+#pragma unroll
+        for (int i = 0; i < TH; ++i) S.e0[c][i] = e[i];
+    }
+    if (lane == 0 || lane == 30) {
+        const int c = lane == 0 ? 0 : 1;
+#pragma unroll
+        for (int i = 0; i < TH; ++i) S.f0[c][i] = fr[i];
+    }
 
     // GGT warm start: raise the source capacities to lambda_k (Section 2.1's
     // monotone case keeps the old flow valid); the newly available source
@@ -334,7 +429,7 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
         const int dl = L[kcur] - L[tl];
 #pragma unroll
         for (int i = 0; i < TH; ++i) {
-            const int sl = __ldg(SLOPE + (size_t)(y0 + i) * pitch + x);
+            const int sl = own ? __ldg(SLOPE + (size_t)(T.y0 + i) * pitch + T.X) : 0;
             e[i] += sl * dl;
             const int m = min(e[i], rt[i]);
             e[i] -= m;
@@ -343,172 +438,183 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
         if (lane == 0) TS->lam = kcur;
     }
 
-    // halo
+    // rows above and below the tile
     int hT = HINF, wvT = 0, fdT = 0, hB = HINF;
-    if (y0 > 0) {
-        const size_t j = (size_t)(y0 - 1) * pitch + x;
+    if (own && T.y0 > 0) {
+        const size_t j = (size_t)(T.y0 - 1) * pitch + T.X;
         hT = __ldcg(Hh + j);
         wvT = __ldg(WV + j);
         fdT = __ldcg(FD + j);
     }
     const int fdT0 = fdT;
-    if (y0 + TH < D.rows) hB = __ldcg(Hh + (size_t)(y0 + TH) * pitch + x);
-    if (lane < TH) {
-        const size_t j = (size_t)(y0 + lane) * pitch;
-        if (x0 > 0) {
-            S.lh[lane] = __ldcg(Hh + j + x0 - 1);
-            S.lw[lane] = __ldg(WH + j + x0 - 1);
-            S.lf[lane] = __ldcg(FR + j + x0 - 1);
-        } else {
-            S.lh[lane] = HINF;
-            S.lw[lane] = 0;
-            S.lf[lane] = 0;
-        }
-        S.lf0[lane] = S.lf[lane];
-        S.lout[lane] = 0;
-        S.rh[lane] = (x0 + TILE_W < pitch) ? __ldcg(Hh + j + x0 + TILE_W) : HINF;
-        S.rout[lane] = 0;
-    }
-    if (lane == 31) {
-#pragma unroll
-        for (int i = 0; i < TH; ++i) S.rf0[i] = fr[i];
-    }
+    if (own && T.y0 + TH < D.rows) hB = __ldcg(Hh + (size_t)(T.y0 + TH) * pitch + T.X);
     __syncwarp();
 
     int outU = 0, outD = 0;
     const int hcap = D.hcap;
-    for (int sw = 0; sw < P.sweeps; ++sw) {
-        // push phase: every active pixel sends excess to t first, then to
-        // lower neighbours along residual arcs; heights are not changed here,
-        // so the two ends of an edge never push against each other
+    unsigned nsw = 0;
+    bool any_act;
+    {
+        bool a = false;
+#pragma unroll
+        for (int i = 0; i < TH; ++i) a |= (e[i] > 0 && h[i] < HINF);
+        any_act = __any_sync(FULL_MASK, a);
+    }
+    const long long c_loaded = P.trace ? clock64() + (e[0] & 0) : 0;
+    for (int sw = 0; sw < P.sweeps && any_act; ++sw) {
+        ++nsw;
+        // Every row of a sweep works from the state at the start of the sweep
+        // (Jacobi order), so the rows are independent.  Heights do not change
+        // during the push phase, so the two ends of an edge never push
+        // against each other.  Push phase: an active pixel sends excess to t
+        // first, then to lower neighbours along residual arcs.
+        int dDa[TH], dUa[TH];
 #pragma unroll
         for (int i = 0; i < TH; ++i) {
             const int hp = h[i];
-            int hL = __shfl_up_sync(FULL_MASK, hp, 1);
-            int hR = __shfl_down_sync(FULL_MASK, hp, 1);
-            int rL = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
-            if (lane == 0) { hL = S.lh[i]; rL = S.lw[i] + S.lf[i]; }
-            if (lane == 31) hR = S.rh[i];
+            const int hL = __shfl_up_sync(FULL_MASK, hp, 1);
+            const int hR = __shfl_down_sync(FULL_MASK, hp, 1);
+            const int rL = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
             const int hU = (i > 0) ? h[i - 1] : hT;
             const int hD = (i < TH - 1) ? h[i + 1] : hB;
             const int rR = wh[i] - fr[i];
             const int rD = wv[i] - fd[i];
             const int rU = (i > 0) ? (wv[i - 1] + fd[i - 1]) : (wvT + fdT);
-            int ex = e[i];
-            int dT = 0, dD = 0, dR = 0, dU = 0, dL = 0;
-            if (ex > 0 && hp < HINF) {
-                dT = min(ex, rt[i]);
-                ex -= dT;
-                if (ex > 0 && rD > 0 && hD < hp) { dD = min(ex, rD); ex -= dD; }
-                if (ex > 0 && rR > 0 && hR < hp) { dR = min(ex, rR); ex -= dR; }
-                if (ex > 0 && rU > 0 && hU < hp) { dU = min(ex, rU); ex -= dU; }
-                if (ex > 0 && rL > 0 && hL < hp) { dL = min(ex, rL); ex -= dL; }
-            }
-            e[i] = ex;
+            const bool a = own && e[i] > 0 && hp < HINF;
+            int ex = a ? e[i] : 0;
+            const int dT = min(ex, rt[i]);
+            ex -= dT;
+            const int dD = (rD > 0 && hD < hp) ? min(ex, rD) : 0;
+            ex -= dD;
+            const int dR = (rR > 0 && hR < hp) ? min(ex, rR) : 0;
+            ex -= dR;
+            const int dU = (rU > 0 && hU < hp) ? min(ex, rU) : 0;
+            ex -= dU;
+            const int dL = (rL > 0 && hL < hp) ? min(ex, rL) : 0;
+            e[i] -= dT + dD + dR + dU + dL;
             rt[i] -= dT;
+            dDa[i] = dD;
+            dUa[i] = dU;
+            // horizontal transfers stay inside the row (ghost lanes collect
+            // what crosses the tile's left and right borders)
             fr[i] += dR;
-            fd[i] += dD;
-            if (i < TH - 1) e[i + 1] += dD; else outD += dD;
-            if (i > 0) { e[i - 1] += dU; fd[i - 1] -= dU; } else { outU += dU; fdT -= dU; }
             const int inR = __shfl_up_sync(FULL_MASK, dR, 1);
             const int inL = __shfl_down_sync(FULL_MASK, dL, 1);
-            if (lane > 0) e[i] += inR;
-            if (lane < 31) { e[i] += inL; fr[i] -= inL; }
-            if (lane == 31) S.rout[i] += dR;
-            if (lane == 0) { S.lf[i] -= dL; S.lout[i] += dL; }
+            e[i] += (lane > 0 ? inR : 0) + (lane < 31 ? inL : 0);
+            fr[i] -= (lane < 31 ? inL : 0);
+        }
+        // vertical transfers, after every row has decided
+#pragma unroll
+        for (int i = 0; i < TH; ++i) {
+            fd[i] += dDa[i];
+            if (i < TH - 1) e[i + 1] += dDa[i]; else outD += dDa[i];
+            if (i > 0) { e[i - 1] += dUa[i]; fd[i - 1] -= dUa[i]; } else { outU += dUa[i]; fdT -= dUa[i]; }
         }
         // relabel phase: an active pixel without an admissible arc moves to
-        // one above its lowest residual neighbour (t has label 0)
+        // one above its lowest residual neighbour (t has label 0); all rows
+        // read the heights of the start of the sweep
+        int hn[TH];
         bool act = false;
 #pragma unroll
         for (int i = 0; i < TH; ++i) {
             const int hp = h[i];
-            int hL = __shfl_up_sync(FULL_MASK, hp, 1);
-            int hR = __shfl_down_sync(FULL_MASK, hp, 1);
-            int rL = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
-            if (lane == 0) { hL = S.lh[i]; rL = S.lw[i] + S.lf[i]; }
-            if (lane == 31) hR = S.rh[i];
-            if (e[i] > 0 && hp < HINF) {
-                const int hU = (i > 0) ? h[i - 1] : hT;
-                const int hD = (i < TH - 1) ? h[i + 1] : hB;
-                const int rU = (i > 0) ? (wv[i - 1] + fd[i - 1]) : (wvT + fdT);
-                int hmin = HINF;
-                if (rt[i] > 0) hmin = 0;
-                if (wv[i] - fd[i] > 0) hmin = min(hmin, hD);
-                if (wh[i] - fr[i] > 0) hmin = min(hmin, hR);
-                if (rU > 0) hmin = min(hmin, hU);
-                if (rL > 0) hmin = min(hmin, hL);
-                if (hmin >= hp) h[i] = (hmin >= HINF - 1 || hmin + 1 >= hcap) ? HINF : hmin + 1;
-                act |= (h[i] < HINF);
-            }
+            const int hL = __shfl_up_sync(FULL_MASK, hp, 1);
+            const int hR = __shfl_down_sync(FULL_MASK, hp, 1);
+            const int rL = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
+            const int hU = (i > 0) ? h[i - 1] : hT;
+            const int hD = (i < TH - 1) ? h[i + 1] : hB;
+            const int rU = (i > 0) ? (wv[i - 1] + fd[i - 1]) : (wvT + fdT);
+            int hmin = rt[i] > 0 ? 0 : HINF;
+            hmin = (wv[i] - fd[i] > 0) ? min(hmin, hD) : hmin;
+            hmin = (wh[i] - fr[i] > 0) ? min(hmin, hR) : hmin;
+            hmin = (rU > 0) ? min(hmin, hU) : hmin;
+            hmin = (rL > 0) ? min(hmin, hL) : hmin;
+            const bool a = own && e[i] > 0 && hp < HINF;
+            const int nh = (hmin >= HINF - 1 || hmin + 1 >= hcap) ? HINF : hmin + 1;
+            hn[i] = (a && hmin >= hp) ? nh : hp;
+            act |= a && hn[i] < HINF;
         }
-        if (!__any_sync(FULL_MASK, act)) break;
+#pragma unroll
+        for (int i = 0; i < TH; ++i) h[i] = hn[i];
+        any_act = __any_sync(FULL_MASK, act);
     }
 
     // write back; pixels and edges on the tile border as atomic deltas
+    const long long c_swept = P.trace ? clock64() : 0;
     long long srt1 = 0;
-    bool act = false;
+    bool act = false, got_l = false, got_r = false;
 #pragma unroll
     for (int i = 0; i < TH; ++i) {
-        const size_t idx = (size_t)(y0 + i) * pitch + x;
+        const size_t idx = (size_t)(T.y0 + i) * pitch + T.X;
         srt1 += rt[i];
-        act |= (e[i] > 0 && h[i] < HINF);
-        const bool perim = (i == 0) || (i == TH - 1) || lane == 0 || lane == 31;
-        if (perim) {
-            const int d = e[i] - e0[i];
-            if (d) atomicAdd(E + idx, d);
-        } else {
-            __stcg(E + idx, e[i]);
-        }
-        __stcg(Hh + idx, h[i]);
-        __stcg(RT + idx, rt[i]);
-        if (lane == 31) {
-            const int d = fr[i] - S.rf0[i];
-            if (d) atomicAdd(FR + idx, d);
-        } else {
-            __stcg(FR + idx, fr[i]);
-        }
-        if (i == TH - 1) {
-            const int d = fd[i] - fd0b;
-            if (d) atomicAdd(FD + idx, d);
-        } else {
-            __stcg(FD + idx, fd[i]);
+        act |= own && (e[i] > 0 && h[i] < HINF);
+        if (own) {
+            int e0 = e[i];
+            bool perim = true;
+            if (lane == 1) e0 = S.e0[0][i];
+            else if (lane == 30) e0 = S.e0[1][i];
+            else if (i == 0) e0 = e0top;
+            else if (i == TH - 1) e0 = e0bot;
+            else perim = false;
+            if (perim) {
+                if (e[i] != e0) atomicAdd(E + idx, e[i] - e0);
+            } else {
+                __stcg(E + idx, e[i]);
+            }
+            __stcg(Hh + idx, h[i]);
+            __stcg(RT + idx, rt[i]);
+            if (lane == 30) {
+                if (fr[i] != S.f0[1][i]) atomicAdd(FR + idx, fr[i] - S.f0[1][i]);
+            } else {
+                __stcg(FR + idx, fr[i]);
+            }
+            if (i == TH - 1) {
+                if (fd[i] != fd0b) atomicAdd(FD + idx, fd[i] - fd0b);
+            } else {
+                __stcg(FD + idx, fd[i]);
+            }
+        } else if (T.inb) {
+            // ghost lane: excess pushed across the border, and (left) the
+            // flow on the left border edge, owned by the neighbour's pixel
+            if (e[i]) {
+                atomicAdd(E + idx, e[i]);
+                if (lane == 0) got_l = true; else got_r = true;
+            }
+            if (lane == 0 && fr[i] != S.f0[0][i]) atomicAdd(FR + idx, fr[i] - S.f0[0][i]);
         }
     }
-    if (y0 > 0) {
-        const size_t j = (size_t)(y0 - 1) * pitch + x;
+    if (own && T.y0 > 0) {
+        const size_t j = (size_t)(T.y0 - 1) * pitch + T.X;
         if (outU) atomicAdd(E + j, outU);
         if (fdT != fdT0) atomicAdd(FD + j, fdT - fdT0);
     }
-    if (outD && y0 + TH < D.rows) atomicAdd(E + (size_t)(y0 + TH) * pitch + x, outD);
-    __syncwarp();
-    bool lo = false, ro = false;
-    if (lane < TH) {
-        const size_t j = (size_t)(y0 + lane) * pitch;
-        if (x0 > 0) {
-            if (S.lout[lane]) { atomicAdd(E + j + x0 - 1, S.lout[lane]); lo = true; }
-            if (S.lf[lane] != S.lf0[lane]) atomicAdd(FR + j + x0 - 1, S.lf[lane] - S.lf0[lane]);
-        }
-        if (S.rout[lane] && x0 + TILE_W < pitch) { atomicAdd(E + j + x0 + TILE_W, S.rout[lane]); ro = true; }
-    }
+    if (own && outD && T.y0 + TH < D.rows) atomicAdd(E + (size_t)(T.y0 + TH) * pitch + T.X, outD);
     unsigned nb = 0;
     if (__any_sync(FULL_MASK, outU > 0)) nb |= 1;
     if (__any_sync(FULL_MASK, outD > 0)) nb |= 2;
-    if (__any_sync(FULL_MASK, lo)) nb |= 4;
-    if (__any_sync(FULL_MASK, ro)) nb |= 8;
+    if (__any_sync(FULL_MASK, got_l)) nb |= 4;
+    if (__any_sync(FULL_MASK, got_r)) nb |= 8;
     nbmask = nb;
     self_active = __any_sync(FULL_MASK, act);
 
     long long df = srt0 - srt1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) df += __shfl_down_sync(FULL_MASK, df, o);
+    if (P.trace) {
+        __threadfence();
+        const long long c_end = clock64();
+        if (lane == 0) {
+            atomicAdd(&P.g->prof[5], (unsigned long long)(c_loaded - c_start));
+            atomicAdd(&P.g->prof[6], (unsigned long long)(c_swept - c_loaded));
+            atomicAdd(&P.g->prof[7], (unsigned long long)(c_end - c_swept));
+        }
+    }
     if (lane == 0) {
+        if (P.trace) atomicAdd(&P.g->prof[4], (unsigned long long)nsw);
         if (df) atomicAdd(&P.ist[inst].flow, (unsigned long long)df);
-        atomicAdd(&P.ist[inst].pr_visits, 1ULL);
-        atomicAdd(&P.ist[inst].visits_step, 1ULL);
-        const int since = atomicAdd(&P.ist[inst].pr_since, 1) + 1;
-        if ((long long)since * 100 >= (long long)P.relabel_pct * D.n_tiles)
-            P.ist[inst].want_bfs = 1;
+        const unsigned long long v = atomicAdd(&P.ist[inst].pr_visits, 1ULL) + 1;
+        const long long since = (long long)(v - *(volatile unsigned long long *)&P.ist[inst].pr_mark);
+        if (since * 100 >= (long long)P.relabel_pct * D.n_tiles) P.ist[inst].want_bfs = 1;
     }
 }
 
@@ -521,10 +627,10 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
 template <int TH>
 __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, const DevInst &D,
                           int epoch, int kcur, bool &self_again, unsigned &nbmask) {
-    const int lane = threadIdx.x & 31;
-    const int lt = g - D.tile_base;
-    const int ty = lt / D.tiles_x, tx = lt - ty * D.tiles_x;
-    const int x0 = tx * TILE_W, y0 = ty * TH, x = x0 + lane;
+    (void)S;
+    const TileGeo T = tile_geo(g, D, TH);
+    const int lane = T.lane;
+    const bool own = T.inb && !T.ghost;
     const int pitch = D.pitch;
     const size_t PS = (size_t)D.rows * pitch;
     int *base = P.planes + D.plane_off;
@@ -535,52 +641,43 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     const int *WV = WH + PS;
     TileState *TS = P.tiles + g;
 
+    // labels of a neighbouring tile count only once it has been visited in
+    // this relabel epoch (otherwise they are left over from push/relabel)
     const bool own_valid = ldv(&TS->epoch) == epoch;
-    const bool vT = ty > 0 && ldv(&P.tiles[g - D.tiles_x].epoch) == epoch;
-    const bool vB = ty < D.tiles_y - 1 && ldv(&P.tiles[g + D.tiles_x].epoch) == epoch;
-    const bool vL = tx > 0 && ldv(&P.tiles[g - 1].epoch) == epoch;
-    const bool vR = tx < D.tiles_x - 1 && ldv(&P.tiles[g + 1].epoch) == epoch;
+    const bool vT = T.ty > 0 && ldv(&P.tiles[g - D.tiles_x].epoch) == epoch;
+    const bool vB = T.ty < D.tiles_y - 1 && ldv(&P.tiles[g + D.tiles_x].epoch) == epoch;
+    bool vX = own_valid;
+    if (lane == 0) vX = T.tx > 0 && ldv(&P.tiles[g - 1].epoch) == epoch;
+    if (lane == 31) vX = T.tx < D.tiles_x - 1 && ldv(&P.tiles[g + 1].epoch) == epoch;
     __threadfence();
 
     int fr[TH], fd[TH], wh[TH], wv[TH], d[TH], dold[TH];
-    unsigned epos = 0, rtpos = 0;
+    unsigned epos = 0;
 #pragma unroll
     for (int i = 0; i < TH; ++i) {
-        const size_t idx = (size_t)(y0 + i) * pitch + x;
-        if (__ldcg(E + idx) > 0) epos |= 1u << i;
-        if (__ldcg(RT + idx) > 0) rtpos |= 1u << i;
-        fr[i] = __ldcg(FR + idx);
-        fd[i] = __ldcg(FD + idx);
-        wh[i] = __ldg(WH + idx);
-        wv[i] = __ldg(WV + idx);
-        d[i] = own_valid ? __ldcg(Hh + idx) : HINF;
+        const size_t idx = (size_t)(T.y0 + i) * pitch + T.X;
+        const bool ep = own && __ldcg(E + idx) > 0;
+        const bool rp = own && __ldcg(RT + idx) > 0;
+        if (ep) epos |= 1u << i;
+        fr[i] = (T.inb && lane != 31) ? __ldcg(FR + idx) : 0;
+        fd[i] = own ? __ldcg(FD + idx) : 0;
+        wh[i] = (T.inb && lane != 31) ? __ldg(WH + idx) : 0;
+        wv[i] = own ? __ldg(WV + idx) : 0;
+        d[i] = (T.inb && vX) ? __ldcg(Hh + idx) : HINF;
         dold[i] = d[i];
-        if (((rtpos >> i) & 1u) && d[i] > 1) d[i] = 1;
+        if (rp) d[i] = min(d[i], 1);
     }
     int hT = HINF, wvT = 0, fdT = 0, hB = HINF;
-    if (y0 > 0) {
-        const size_t j = (size_t)(y0 - 1) * pitch + x;
+    if (own && T.y0 > 0) {
+        const size_t j = (size_t)(T.y0 - 1) * pitch + T.X;
         wvT = __ldg(WV + j);
         fdT = __ldcg(FD + j);
         if (vT) hT = __ldcg(Hh + j);
     }
-    if (vB) hB = __ldcg(Hh + (size_t)(y0 + TH) * pitch + x);
-    if (lane < TH) {
-        const size_t j = (size_t)(y0 + lane) * pitch;
-        if (x0 > 0) {
-            S.lh[lane] = vL ? __ldcg(Hh + j + x0 - 1) : HINF;
-            S.lw[lane] = __ldg(WH + j + x0 - 1);
-            S.lf[lane] = __ldcg(FR + j + x0 - 1);
-        } else {
-            S.lh[lane] = HINF;
-            S.lw[lane] = 0;
-            S.lf[lane] = 0;
-        }
-        S.rh[lane] = vR ? __ldcg(Hh + j + x0 + TILE_W) : HINF;
-    }
-    __syncwarp();
+    if (own && vB) hB = __ldcg(Hh + (size_t)(T.y0 + TH) * pitch + T.X);
 
     // d(p) <= d(q) + 1 for every residual arc p -> q, relaxed to the fixpoint
+    // (ghost lanes only supply their neighbours' labels)
     bool capped = true;
     for (int it = 0; it < 64 * TH; ++it) {
         bool ch = false;
@@ -588,48 +685,58 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
         for (int i = 0; i < TH; ++i) {          // from the row above (arc p -> up)
             const int up = (i > 0) ? d[i - 1] : hT;
             const int rU = (i > 0) ? (wv[i - 1] + fd[i - 1]) : (wvT + fdT);
-            if (rU > 0 && up + 1 < d[i]) { d[i] = up + 1; ch = true; }
+            const bool b = own && rU > 0 && up + 1 < d[i];
+            d[i] = b ? up + 1 : d[i];
+            ch |= b;
         }
 #pragma unroll
         for (int i = TH - 1; i >= 0; --i) {     // from the row below (arc p -> down)
             const int dn = (i < TH - 1) ? d[i + 1] : hB;
-            if (wv[i] - fd[i] > 0 && dn + 1 < d[i]) { d[i] = dn + 1; ch = true; }
+            const bool b = own && wv[i] - fd[i] > 0 && dn + 1 < d[i];
+            d[i] = b ? dn + 1 : d[i];
+            ch |= b;
         }
+        // horizontal: if no label improves by one step from a horizontal
+        // neighbour, every row is at its horizontal fixpoint; otherwise scan
+        // all rows together (independent, so they overlap)
+        bool imp = false;
 #pragma unroll
         for (int i = 0; i < TH; ++i) {
-            // from the right along runs of residual arcs p -> p+1: segmented
-            // min-plus scan over the warp
-            int v = d[i];
-            int c = (wh[i] - fr[i]) > 0;
-            if (lane == 31 && c && S.rh[i] + 1 < v) v = S.rh[i] + 1;
+            const int dr = __shfl_down_sync(FULL_MASK, d[i], 1);
+            const int dl = __shfl_up_sync(FULL_MASK, d[i], 1);
+            const int rl = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
+            imp |= own && (((wh[i] - fr[i]) > 0 && dr + 1 < d[i]) || (rl > 0 && dl + 1 < d[i]));
+        }
+        if (__any_sync(FULL_MASK, imp)) {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v2 = __shfl_down_sync(FULL_MASK, v, o);
-                const int c2 = __shfl_down_sync(FULL_MASK, c, o);
-                if (lane + o < 32) {
-                    if (c && v2 + o < v) v = v2 + o;
-                    c = c & c2;
-                } else {
-                    c = 0;
-                }
-            }
-            // from the left along runs of residual arcs p -> p-1
-            int rl = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
-            if (lane == 0) rl = S.lw[i] + S.lf[i];
-            int c3 = rl > 0;
-            if (lane == 0 && c3 && S.lh[i] + 1 < v) v = S.lh[i] + 1;
+            for (int i = 0; i < TH; ++i) {
+                // from the right along runs of residual arcs p -> p+1: a
+                // segmented min-plus scan over the warp
+                int v = d[i];
+                int c = own && (wh[i] - fr[i]) > 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v2 = __shfl_up_sync(FULL_MASK, v, o);
-                const int c2 = __shfl_up_sync(FULL_MASK, c3, o);
-                if (lane >= o) {
-                    if (c3 && v2 + o < v) v = v2 + o;
-                    c3 = c3 & c2;
-                } else {
-                    c3 = 0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v2 = __shfl_down_sync(FULL_MASK, v, o);
+                    const int c2 = __shfl_down_sync(FULL_MASK, c, o);
+                    const bool ok = lane + o < 32;
+                    v = (ok && c && v2 + o < v) ? v2 + o : v;
+                    c = ok ? (c & c2) : 0;
                 }
+                // from the left along runs of residual arcs p -> p-1
+                const int rl = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
+                int c3 = own && rl > 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v2 = __shfl_up_sync(FULL_MASK, v, o);
+                    const int c2 = __shfl_up_sync(FULL_MASK, c3, o);
+                    const bool ok = lane >= o;
+                    v = (ok && c3 && v2 + o < v) ? v2 + o : v;
+                    c3 = ok ? (c3 & c2) : 0;
+                }
+                const bool b = own && v < d[i];
+                d[i] = b ? v : d[i];
+                ch |= b;
             }
-            if (v < d[i]) { d[i] = v; ch = true; }
         }
         if (!__any_sync(FULL_MASK, ch)) { capped = false; break; }
     }
@@ -639,17 +746,16 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     // than the neighbour q could have read, q -> p is residual and q's label
     // is above d(p) + 1
     bool wT = false, wB = false, wL = false, wR = false;
-    if (y0 > 0) wT = d[0] < dold[0] && (wvT - fdT) > 0 && d[0] + 1 < hT;
-    if (ty < D.tiles_y - 1) wB = d[TH - 1] < dold[TH - 1] && (wv[TH - 1] + fd[TH - 1]) > 0 && d[TH - 1] + 1 < hB;
-    if (lane == 0 && tx > 0) {
+    if (own && T.y0 > 0) wT = d[0] < dold[0] && (wvT - fdT) > 0 && d[0] + 1 < hT;
+    if (own && T.ty < D.tiles_y - 1) wB = d[TH - 1] < dold[TH - 1] && (wv[TH - 1] + fd[TH - 1]) > 0 && d[TH - 1] + 1 < hB;
 #pragma unroll
-        for (int i = 0; i < TH; ++i)
-            wL |= d[i] < dold[i] && (S.lw[i] - S.lf[i]) > 0 && d[i] + 1 < S.lh[i];
-    }
-    if (lane == 31 && tx < D.tiles_x - 1) {
-#pragma unroll
-        for (int i = 0; i < TH; ++i)
-            wR |= d[i] < dold[i] && (wh[i] + fr[i]) > 0 && d[i] + 1 < S.rh[i];
+    for (int i = 0; i < TH; ++i) {
+        const int qd_l = __shfl_up_sync(FULL_MASK, d[i], 1);              // lane 0's label, seen by lane 1
+        const int qr_l = __shfl_up_sync(FULL_MASK, wh[i] - fr[i], 1);     // residual lane0 -> lane1
+        const int qd_r = __shfl_down_sync(FULL_MASK, d[i], 1);            // lane 31's label, seen by lane 30
+        const bool imp_i = d[i] < dold[i];
+        wL |= own && lane == 1 && T.tx > 0 && imp_i && qr_l > 0 && d[i] + 1 < qd_l;
+        wR |= own && lane == 30 && T.tx < D.tiles_x - 1 && imp_i && (wh[i] + fr[i]) > 0 && d[i] + 1 < qd_r;
     }
     unsigned nb = 0;
     if (__any_sync(FULL_MASK, wT)) nb |= 1;
@@ -663,9 +769,11 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     int cnt = 0;
 #pragma unroll
     for (int i = 0; i < TH; ++i) {
-        const size_t idx = (size_t)(y0 + i) * pitch + x;
-        __stcg(Hh + idx, d[i]);
-        M[idx] = d[i] >= HINF ? 1 : 0;
+        const size_t idx = (size_t)(T.y0 + i) * pitch + T.X;
+        if (own) {
+            __stcg(Hh + idx, d[i]);
+            M[idx] = d[i] >= HINF ? 1 : 0;
+        }
         cnt += __popc(__ballot_sync(FULL_MASK, ((epos >> i) & 1u) && d[i] < HINF));
     }
     __threadfence();
@@ -676,7 +784,6 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
         TS->active = cnt;
         if (cnt != old) atomicAdd(&P.ist[inst].active, cnt - old);
         atomicAdd(&P.ist[inst].bfs_visits, 1ULL);
-        atomicAdd(&P.ist[inst].visits_step, 1ULL);
     }
 }
 
@@ -690,35 +797,46 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32) worker_kernel(const __grid_
     __shared__ WarpSmem<TH> smem[WORKER_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<TH> &S = smem[w];
+    const int round_mode = ldv(&P.g->round_mode);
+    const bool prof = P.trace != nullptr;
+    unsigned long long tw = 0, tpr = 0, tbfs = 0, tfin = 0, t0 = prof ? gtime_ns() : 0;
     for (;;) {
         int g = 0;
-        if (lane == 0) g = ring_pop(P);
+        if (lane == 0) g = round_mode ? ring_pop_round(P) : ring_pop_ticket(P);
         g = __shfl_sync(FULL_MASK, g, 0);
+        if (prof) { const unsigned long long t1 = gtime_ns(); tw += t1 - t0; t0 = t1; }
         if (g < 0) break;
-        const int inst = P.tile_inst[g];
-        const DevInst D = P.inst[inst];
-        volatile InstState *IS = P.ist + inst;
-        int phase = 0, status = 0, epoch = 0, k = 0;
+        const int inst = __ldg(P.tile_inst + g);
         if (lane == 0) {
             atomicExch(&P.tiles[g].state, T_RUNNING);
             __threadfence();
-            phase = IS->phase;
-            status = IS->status;
-            epoch = IS->epoch;
-            k = IS->k;
         }
-        phase = __shfl_sync(FULL_MASK, phase, 0);
-        status = __shfl_sync(FULL_MASK, status, 0);
-        epoch = __shfl_sync(FULL_MASK, epoch, 0);
-        k = __shfl_sync(FULL_MASK, k, 0);
         __syncwarp();
+        const DevInst D = load_inst(P, inst);
+        // phase, k, epoch, status in one 16-byte load
+        int phase, k, epoch, status;
+        asm volatile("ld.volatile.global.v4.s32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(phase), "=r"(k), "=r"(epoch), "=r"(status)
+                     : "l"(P.ist + inst));
         bool requeue = false;
         unsigned nb = 0;
         if (status == PMF_OK && phase == PH_PR) pr_visit<TH>(P, S, g, inst, D, k, requeue, nb);
         else if (status == PMF_OK && phase == PH_BFS) bfs_visit<TH>(P, S, g, inst, D, epoch, k, requeue, nb);
         __threadfence();
         __syncwarp();
+        if (prof) {
+            const unsigned long long t1 = gtime_ns();
+            if (phase == PH_PR) tpr += t1 - t0; else tbfs += t1 - t0;
+            t0 = t1;
+        }
         finish(P, g, inst, phase, requeue, nb, D);
+        if (prof) { const unsigned long long t1 = gtime_ns(); tfin += t1 - t0; t0 = t1; }
+    }
+    if (prof && lane == 0) {
+        atomicAdd(&P.g->prof[0], tw);
+        atomicAdd(&P.g->prof[1], tpr);
+        atomicAdd(&P.g->prof[2], tbfs);
+        atomicAdd(&P.g->prof[3], tfin);
     }
 }
 
@@ -795,32 +913,31 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
         s.phase = PH_BFS;
         s.k = 0;
         s.epoch = 1;
+        s.vflags = P.inst_flags[i] | P.img_flags[D.image];
+        s.status = flags_to_status(s.vflags);
+        s.pad0_ = s.pad1_ = s.pad2_ = s.pad3_ = 0;
+        s.pr_mark = 0;
+        s.step_mark = 0;
+        s.epochs = 1;
         s.outstanding = D.n_tiles;
         s.active = 0;
         s.want_bfs = 0;
-        s.vflags = P.inst_flags[i] | P.img_flags[D.image];
-        s.status = flags_to_status(s.vflags);
         s.flow = 0;
-        s.pr_since = 0;
-        s.pad_ = 0;
         s.pr_visits = 0;
         s.bfs_visits = 0;
-        s.epochs = 1;
-        s.visits_step = 0;
         P.ist[i] = s;
     }
     if (t0 == 0) {
-        Globals G;
-        G.head = 0;
-        G.tail = (unsigned long long)P.n_tiles_total;
-        G.round_end = G.tail;
-        G.pending = P.n_tiles_total;
-        G.completed = 0;
-        G.err = 0;
-        G.round_mode = 0;
-        G.items = 0;
-        G.t_start = gtime_ns();
-        *P.g = G;
+        Globals *G = P.g;
+        G->head = 0;
+        G->tail = (unsigned long long)P.n_tiles_total;
+        G->inst_done = 0;
+        G->err = 0;
+        G->round_mode = 0;
+        G->round_end = G->tail;
+        G->t_start = gtime_ns();
+        G->trace_n = 0;
+        for (int j = 0; j < 8; ++j) G->prof[j] = 0;
     }
 }
 
@@ -884,6 +1001,7 @@ cudaError_t launch_pad_image(const Params &P, int image, const DevInst &d, const
     int32_t *wh = const_cast<int32_t *>(P.img) + d.img_off;
     const size_t n = (size_t)d.rows * d.pitch;
     const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    (void)cudaGetLastError();
     pad_image_kernel<<<blocks, 256, 0, s>>>(wh, wh + n, w_h, w_v, d.H, d.W, d.rows, d.pitch, flags);
     return cudaGetLastError();
 }
@@ -893,6 +1011,7 @@ cudaError_t launch_pad_terminals(const Params &P, int inst, const DevInst &d, co
     int32_t *base = P.planes + d.plane_off;
     const size_t n = (size_t)d.rows * d.pitch;
     const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    (void)cudaGetLastError();
     pad_terminals_kernel<<<blocks, 256, 0, s>>>(base + P_SRC0 * n, base + P_SLOPE * n, base + P_CT * n,
                                                 src0, slope, sink, d.H, d.W, d.rows, d.pitch,
                                                 P.inst_flags + inst);
@@ -902,6 +1021,7 @@ cudaError_t launch_pad_terminals(const Params &P, int inst, const DevInst &d, co
 cudaError_t launch_reset(const Params &P, cudaStream_t s) {
     const size_t n = (size_t)P.ring_mask + 1;
     const int blocks = (int)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048);
+    (void)cudaGetLastError();
     reset_kernel<<<blocks, 256, 0, s>>>(P);
     return cudaGetLastError();
 }
@@ -911,17 +1031,20 @@ cudaError_t launch_init(const Params &P, int max_pixels, cudaStream_t s) {
     if (bx > 64) bx = 64;
     if (bx < 1) bx = 1;
     dim3 grid(bx, P.n_inst < 65535 ? P.n_inst : 65535);
+    (void)cudaGetLastError();
     init_kernel<<<grid, 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 
 cudaError_t launch_worker(const Params &P, int grid, cudaStream_t s) {
+    (void)cudaGetLastError();
     if (P.tile_h == 4) worker_kernel<4><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
     else worker_kernel<8><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
     return cudaGetLastError();
 }
 
 cudaError_t launch_begin_round(const Params &P, cudaStream_t s) {
+    (void)cudaGetLastError();
     begin_round_kernel<<<1, 1, 0, s>>>(P.g);
     return cudaGetLastError();
 }

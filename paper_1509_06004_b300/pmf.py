@@ -36,14 +36,21 @@ PMF_MAX_PAIRWISE = (1 << 28) - 1
 # every entry point declared in include/pmf.h
 EXPORTS = ["pmf_workspace_size", "pmf_create_batch", "pmf_set_tuning", "pmf_get_tuning",
            "pmf_set_capacities", "pmf_set_terminals", "pmf_solve_schedule", "pmf_sync",
-           "pmf_get_cut", "pmf_get_flow", "pmf_get_stats", "pmf_get_mask_layout",
-           "pmf_destroy_batch", "pmf_status_string", "pmf_version"]
+           "pmf_get_cut", "pmf_get_flow", "pmf_get_cuts", "pmf_get_flows", "pmf_get_timing",
+           "pmf_get_stats", "pmf_get_trace", "pmf_get_profile", "pmf_get_mask_layout",
+           "pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error"]
 
 
 class PmfError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
-        super().__init__(f"{where}: {status_string(status)} (status {status})")
+        msg = f"{where}: {status_string(status)} (status {status})"
+        if status == PMF_ERR_CUDA:
+            try:
+                msg += f" [{lib().pmf_last_error().decode()}]"
+            except Exception:
+                pass
+        super().__init__(msg)
 
 
 class BatchDesc(ctypes.Structure):
@@ -57,7 +64,17 @@ class Tuning(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("sweeps", ctypes.c_int32),
                 ("relabel_every", ctypes.c_int32), ("max_visits_per_tile", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("trace", ctypes.c_int32),
+                ("poll_ns", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class TraceEvent(ctypes.Structure):
+    _fields_ = [("t_ns", ctypes.c_uint64), ("inst", ctypes.c_int32), ("event", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("epoch", ctypes.c_int32), ("pr_visits", ctypes.c_int64),
+                ("bfs_visits", ctypes.c_int64)]
+
+
+TRACE_EVENTS = {0: "relabel", 1: "step-done", 2: "push-relabel", 3: "done", 4: "not-converged"}
 
 
 class Stats(ctypes.Structure):
@@ -95,6 +112,11 @@ def lib(path: str | None = None):
             L.pmf_get_cut.argtypes = [vp, i32, i32, vp, ctypes.c_int]
             L.pmf_get_flow.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_int64)]
             L.pmf_get_stats.argtypes = [vp, i32, ctypes.POINTER(Stats)]
+            L.pmf_get_cuts.argtypes = [vp, i32, vp, ctypes.c_int]
+            L.pmf_get_flows.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64)]
+            L.pmf_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+            L.pmf_get_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+            L.pmf_get_trace.argtypes = [vp, ctypes.POINTER(TraceEvent), i32, i32p]
             L.pmf_get_mask_layout.argtypes = [vp, i32, ctypes.POINTER(vp), i32p, i32p]
             L.pmf_destroy_batch.argtypes = [vp]
             L.pmf_destroy_batch.restype = None
@@ -102,8 +124,10 @@ def lib(path: str | None = None):
             L.pmf_status_string.restype = ctypes.c_char_p
             L.pmf_version.argtypes = []
             L.pmf_version.restype = ctypes.c_char_p
+            L.pmf_last_error.argtypes = []
+            L.pmf_last_error.restype = ctypes.c_char_p
             for name in EXPORTS:
-                if name not in ("pmf_destroy_batch", "pmf_status_string", "pmf_version"):
+                if name not in ("pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error"):
                     getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -217,7 +241,7 @@ class Batch:
     def tuning(self) -> dict:
         t = Tuning()
         _check(lib().pmf_get_tuning(self._h, ctypes.byref(t)), "pmf_get_tuning")
-        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+        return {f: getattr(t, f) for f, _ in Tuning._fields_ if f != "reserved"}
 
     # -- solve -------------------------------------------------------------------
     def solve(self, lambdas, stream=None):
@@ -262,14 +286,51 @@ class Batch:
         return out
 
     def flows(self, inst: int) -> np.ndarray:
-        return np.array([self.get_flow(inst, k) for k in range(self.n_lambda)], np.int64)
-
-    def cuts(self, inst: int) -> np.ndarray:
-        H, W = self.shapes[self.inst_image[inst]]
-        out = np.empty((self.n_lambda, H, W), np.uint8)
-        for k in range(self.n_lambda):
-            self.get_cut(inst, k, out[k])
+        out = np.empty(self.n_lambda, np.int64)
+        _check(lib().pmf_get_flows(self._h, int(inst), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+               "pmf_get_flows")
         return out
+
+    def cuts(self, inst: int, out=None) -> np.ndarray:
+        """All masks of an instance, [n_lambda, H, W] (numpy host array, or a
+        contiguous uint8 CUDA tensor for a device copy)."""
+        H, W = self.shapes[self.inst_image[inst]]
+        if out is None:
+            out = np.empty((self.n_lambda, H, W), np.uint8)
+        try:
+            import torch
+            if isinstance(out, torch.Tensor):
+                assert out.is_cuda and out.dtype == torch.uint8 and out.is_contiguous()
+                assert out.numel() == self.n_lambda * H * W
+                _check(lib().pmf_get_cuts(self._h, int(inst), ctypes.c_void_p(out.data_ptr()), 1), "pmf_get_cuts")
+                return out
+        except ImportError:
+            pass
+        assert out.dtype == np.uint8 and out.flags.c_contiguous and out.size == self.n_lambda * H * W
+        _check(lib().pmf_get_cuts(self._h, int(inst), ctypes.c_void_p(out.ctypes.data), 0), "pmf_get_cuts")
+        return out
+
+    def timing(self) -> tuple[float, float]:
+        """(solve_ms, worker_ms) of the last solve, from library-recorded CUDA events."""
+        a, w = ctypes.c_float(0), ctypes.c_float(0)
+        _check(lib().pmf_get_timing(self._h, ctypes.byref(a), ctypes.byref(w)), "pmf_get_timing")
+        return float(a.value), float(w.value)
+
+    def trace(self) -> list[dict]:
+        """Phase-change events of the last solve (needs set_tuning(trace=1))."""
+        n = ctypes.c_int32(0)
+        _check(lib().pmf_get_trace(self._h, None, 0, ctypes.byref(n)), "pmf_get_trace")
+        buf = (TraceEvent * max(1, n.value))()
+        _check(lib().pmf_get_trace(self._h, buf, n.value, ctypes.byref(n)), "pmf_get_trace")
+        return [{f: getattr(buf[i], f) for f, _ in TraceEvent._fields_} for i in range(n.value)]
+
+    def profile(self) -> dict:
+        """Warp-time breakdown of the last solve (needs set_tuning(trace=1))."""
+        a = (ctypes.c_uint64 * 8)()
+        _check(lib().pmf_get_profile(self._h, a), "pmf_get_profile")
+        keys = ["wait_ns", "pr_ns", "bfs_ns", "retire_ns", "sweeps", "pr_load_cyc", "pr_sweep_cyc",
+                "pr_store_cyc"]
+        return {k: int(a[i]) for i, k in enumerate(keys)}
 
     def stats(self, inst: int) -> dict:
         s = Stats()
