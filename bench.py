@@ -253,14 +253,22 @@ def run_ours(args, rank, world, dev):
 
 
 def _profiled_traffic(args, wl):
-    """DRAM bytes per worker launch from the committed ncu summary, if one
-    matches this workload and mode (None otherwise)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per worker launch from the committed ncu summary
+    (profiles/worker_kernel_traffic.txt) when it was taken on the current
+    kernel source and matches this workload and mode; None otherwise."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "worker_kernel_traffic.txt")
+    src = os.path.join(ROOT, "paper_1509_06004_b300", "csrc", "pmf_kernels.cu")
     try:
-        d = json.load(open(p))
-        return d.get(f"{wl.name}|{args.mode}")
-    except (OSError, ValueError):
+        lines = [l.strip() for l in open(p) if l.strip() and not l.startswith("#")]
+        cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
         return None
+    kv = dict(l.rsplit(":", 1) for l in lines)
+    if kv.get("kernel_sha256_16", "").strip() != cur:
+        return None
+    v = kv.get(f"{wl.name}|{args.mode}")
+    return float(v) if v is not None else None
 
 
 def per_solve_launch(args, wl, dev, pmf):
