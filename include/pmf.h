@@ -219,6 +219,51 @@ PMF_API void pmf_destroy_batch(pmf_batch *b);
 
 PMF_API const char *pmf_status_string(pmf_status s);
 
+/* ------------------------------------------------------------------------ */
+/* Solve without allocating (the paper has no counterpart: this entry point   */
+/* exists for callers of this library, not for the method).                   */
+/* ------------------------------------------------------------------------ */
+#define PMF_NOALLOC_SCRATCH_MB 24      /* device memory reserved for it when the library loads */
+#define PMF_NOALLOC_MAX_PIXELS 262144  /* limit on rows*pitch: rows = H rounded up to 16,
+                                          pitch = W rounded up to 32 (e.g. 512 x 512) */
+#define PMF_NOALLOC_MAX_LAMBDAS 32     /* limit on the schedule length */
+
+/* One instance (one image, one set of terminal capacities, its lambda
+ * schedule) solved with no memory allocation of any kind: no cudaMalloc,
+ * cudaFree, pinned or pool allocation, no allocating library routine.  It is
+ * meant for callers that cannot allocate device memory themselves or let a
+ * library do it: code inside a host framework that owns the whole device
+ * memory budget and hands out only pre-reserved buffers, and latency-critical
+ * paths where cudaMalloc's implicit device-wide synchronisation is not
+ * acceptable.  All scratch (state planes, masks, work queue) lives in one
+ * fixed device array of PMF_NOALLOC_SCRATCH_MB MiB that every GPU using the
+ * library holds until the process exits.
+ *
+ * Inputs: w_h, w_v, src0, slope, sink are DEVICE pointers to H*W int32 arrays
+ * (same meaning as pmf_set_capacities / pmf_set_terminals); lambdas is a HOST
+ * array of n_lambda nondecreasing values.  Outputs: masks is a DEVICE buffer
+ * of n_lambda*H*W bytes ([k][y][x], 1 = source side), flows a HOST array of
+ * n_lambda int64 values.  Runs on cuda_stream (a cudaStream_t, NULL = legacy
+ * default stream) on the current device and returns when the results are in
+ * place.
+ *
+ * Errors: sizes beyond PMF_NOALLOC_MAX_PIXELS or PMF_NOALLOC_MAX_LAMBDAS give
+ * PMF_ERR_OUT_OF_MEMORY before any GPU work; a decreasing schedule gives
+ * PMF_ERR_NOT_MONOTONE; invalid capacities give the statuses pmf_sync reports
+ * for a batch.
+ *
+ * The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  The array is shared by all calls and keeps the last call's
+ * contents; every call re-initialises what must start from zero.  Calls whose
+ * GPU work overlapped would race on the shared array, so calls from different
+ * host threads are serialised by a process-wide lock held until the call's
+ * GPU work has finished. */
+PMF_API pmf_status pmf_solve_noalloc(int32_t H, int32_t W, const int32_t *w_h, const int32_t *w_v,
+                                     const int32_t *src0, const int32_t *slope, const int32_t *sink,
+                                     const int32_t *lambdas, int32_t n_lambda, uint8_t *masks,
+                                     int64_t *flows, void *cuda_stream);
+
 /* Text of the last CUDA failure seen by this thread ("" if none): the call
  * site and cudaGetErrorString, for diagnostics after PMF_ERR_CUDA. */
 PMF_API const char *pmf_last_error(void);

@@ -1,0 +1,171 @@
+// pmf_solve_noalloc: a single-instance solve that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: code running inside a host framework
+// that owns the whole device-memory budget and hands out only pre-reserved
+// buffers, or latency-critical paths where cudaMalloc's implicit device-wide
+// synchronisation is not allowed.  For them this entry point keeps all the
+// solver's scratch (state planes, masks, queue, tile and instance records) in a
+// fixed, file-scope device array that the library reserves when it is loaded;
+// the caller passes only its input capacities and its output buffers.
+//
+// The array is shared by every call in the process and keeps the last call's
+// contents; each call re-initialises the parts that must start from zero.  Two
+// calls whose GPU work overlapped would race on the array, so calls are
+// serialised by a process-wide lock held until the call's stream work is done.
+#include <cstring>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "pmf.h"
+#include "pmf_internal.h"
+
+using namespace pmf;
+
+// the scratch: every GPU that loads the library holds it until exit
+static __device__ __align__(256) unsigned char g_noalloc_scratch[(size_t)PMF_NOALLOC_SCRATCH_MB << 20];
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)PMF_NOALLOC_SCRATCH_MB << 20;
+constexpr int kMaxDevices = 64;
+constexpr int kTileH = 8;
+
+std::mutex g_lock;
+void *g_addr[kMaxDevices];   // device address of the array, per device, looked up once
+
+size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+// the array's device address on the current device (set-up on first use)
+pmf_status scratch_address(int dev, char **out) {
+    if (dev < 0 || dev >= kMaxDevices) return PMF_ERR_INVALID_ARG;
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) return PMF_ERR_CUDA;
+        g_addr[dev] = p;
+    }
+    *out = static_cast<char *>(g_addr[dev]);
+    return PMF_OK;
+}
+
+}  // namespace
+
+extern "C" PMF_API pmf_status pmf_solve_noalloc(int32_t H, int32_t W, const int32_t *w_h,
+                                                const int32_t *w_v, const int32_t *src0,
+                                                const int32_t *slope, const int32_t *sink,
+                                                const int32_t *lambdas, int32_t n_lambda,
+                                                uint8_t *masks, int64_t *flows, void *cuda_stream) {
+    if (H < 1 || W < 1 || !w_h || !w_v || !src0 || !slope || !sink || !lambdas || !masks || !flows)
+        return PMF_ERR_INVALID_ARG;
+    if (n_lambda < 1) return PMF_ERR_INVALID_ARG;
+    for (int k = 1; k < n_lambda; ++k)
+        if (lambdas[k] < lambdas[k - 1]) return PMF_ERR_NOT_MONOTONE;
+    const int rows = (H + ROW_ALIGN - 1) / ROW_ALIGN * ROW_ALIGN;
+    const int pitch = (W + TILE_W - 1) / TILE_W * TILE_W;
+    const size_t PS = (size_t)rows * pitch;
+    // stated limits (see pmf.h)
+    if (PS > (size_t)PMF_NOALLOC_MAX_PIXELS || n_lambda > PMF_NOALLOC_MAX_LAMBDAS) return PMF_ERR_OUT_OF_MEMORY;
+
+    // layout inside the array
+    const int tiles_x = (W + TILE_IN - 1) / TILE_IN, tiles_y = rows / kTileH;
+    const int n_tiles = tiles_x * tiles_y;
+    size_t ring_cap = 1;
+    while (ring_cap < (size_t)n_tiles + 16384) ring_cap <<= 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = up256(off + bytes); return o; };
+    const size_t o_img = take(PS * 4 * N_IMG_PLANES);
+    const size_t o_inst = take(PS * 4 * N_INST_PLANES);
+    const size_t o_masks = take(PS * (size_t)n_lambda);
+    const size_t o_dinst = take(sizeof(DevInst));
+    const size_t o_ist = take(sizeof(InstState));
+    const size_t o_tiles = take(sizeof(TileState) * n_tiles);
+    const size_t o_tinst = take(sizeof(int32_t) * n_tiles);
+    const size_t o_ring = take(sizeof(int32_t) * ring_cap);
+    const size_t o_lam = take(sizeof(int32_t) * n_lambda);
+    const size_t o_flows = take(sizeof(int64_t) * n_lambda);
+    const size_t o_glob = take(sizeof(Globals));
+    const size_t o_flags = take(sizeof(int32_t) * 2);
+    if (off > kScratchBytes) return PMF_ERR_OUT_OF_MEMORY;
+
+    std::lock_guard<std::mutex> guard(g_lock);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PMF_ERR_CUDA;
+    char *ws = nullptr;
+    pmf_status st = scratch_address(dev, &ws);
+    if (st != PMF_OK) return st;
+    int n_sm = 0, bps = 0;
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1)
+        return PMF_ERR_CUDA;
+    if (worker_occupancy(kTileH, &bps) != cudaSuccess || bps < 1) bps = 1;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+    DevInst d;
+    std::memset(&d, 0, sizeof(d));
+    d.H = H;
+    d.W = W;
+    d.pitch = pitch;
+    d.rows = rows;
+    d.tiles_x = tiles_x;
+    d.tiles_y = tiles_y;
+    d.n_tiles = n_tiles;
+    d.n_lambda = n_lambda;
+    d.hcap = H * W + 1;
+
+    Params P;
+    std::memset(&P, 0, sizeof(P));
+    P.trace = nullptr;
+    P.planes = reinterpret_cast<int32_t *>(ws + o_inst);
+    P.img = reinterpret_cast<const int32_t *>(ws + o_img);
+    P.masks = reinterpret_cast<uint8_t *>(ws + o_masks);
+    P.inst = reinterpret_cast<const DevInst *>(ws + o_dinst);
+    P.ist = reinterpret_cast<InstState *>(ws + o_ist);
+    P.tiles = reinterpret_cast<TileState *>(ws + o_tiles);
+    P.tile_inst = reinterpret_cast<const int32_t *>(ws + o_tinst);
+    P.ring = reinterpret_cast<int32_t *>(ws + o_ring);
+    P.lambdas = reinterpret_cast<const int32_t *>(ws + o_lam);
+    P.flows = reinterpret_cast<long long *>(ws + o_flows);
+    P.g = reinterpret_cast<Globals *>(ws + o_glob);
+    P.img_flags = reinterpret_cast<const int32_t *>(ws + o_flags);
+    P.inst_flags = reinterpret_cast<int32_t *>(ws + o_flags) + 1;
+    P.ring_mask = (unsigned long long)(ring_cap - 1);
+    P.n_inst = 1;
+    P.n_tiles_total = n_tiles;
+    P.max_lambdas = n_lambda;
+    P.sweeps = 8;
+    P.relabel_pct = 200;
+    P.tile_h = kTileH;
+    P.poll_ns = 256;
+    P.max_visits_per_tile = 2000;
+    P.stall_ns = 5000000000LL;
+    P.max_ns = 120000000000LL;
+
+    // everything the solve reads before writing starts from zero; the rest is
+    // written in full by the set-up kernels
+    cudaError_t e = cudaMemsetAsync(ws + o_flags, 0, sizeof(int32_t) * 2, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + o_glob, 0, sizeof(Globals), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + o_flows, 0, sizeof(int64_t) * n_lambda, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws + o_dinst, &d, sizeof(d), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws + o_lam, lambdas, sizeof(int32_t) * n_lambda, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_pad_image(P, 0, d, w_h, w_v, reinterpret_cast<int32_t *>(ws + o_flags), s);
+    if (e == cudaSuccess) e = launch_pad_terminals(P, 0, d, src0, slope, sink, s);
+    if (e == cudaSuccess) e = launch_reset(P, s);
+    if (e == cudaSuccess) e = launch_init(P, (int)PS, s);
+    if (e == cudaSuccess) e = launch_worker(P, bps * n_sm, s);
+    InstState ist;
+    Globals glob;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ist, ws + o_ist, sizeof(ist), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&glob, ws + o_glob, sizeof(glob), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return PMF_ERR_CUDA;
+    if (ist.status != PMF_OK) return (pmf_status)ist.status;
+    if (glob.err || ist.phase != PH_DONE || ist.k < n_lambda) return PMF_ERR_NOT_CONVERGED;
+
+    // outputs: flow values to the caller's host array, masks to its device buffer
+    e = cudaMemcpyAsync(flows, ws + o_flows, sizeof(int64_t) * n_lambda, cudaMemcpyDeviceToHost, s);
+    for (int k = 0; k < n_lambda && e == cudaSuccess; ++k)
+        e = cudaMemcpy2DAsync(masks + (size_t)k * H * W, W, ws + o_masks + (size_t)k * PS, pitch, W, H,
+                              cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? PMF_OK : PMF_ERR_CUDA;
+}

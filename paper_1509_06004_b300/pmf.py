@@ -38,7 +38,8 @@ EXPORTS = ["pmf_workspace_size", "pmf_create_batch", "pmf_set_tuning", "pmf_get_
            "pmf_set_capacities", "pmf_set_terminals", "pmf_solve_schedule", "pmf_sync",
            "pmf_get_cut", "pmf_get_flow", "pmf_get_cuts", "pmf_get_flows", "pmf_get_timing",
            "pmf_get_stats", "pmf_get_trace", "pmf_get_profile", "pmf_get_mask_layout",
-           "pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error"]
+           "pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error",
+           "pmf_solve_noalloc"]
 
 
 class PmfError(RuntimeError):
@@ -124,6 +125,8 @@ def lib(path: str | None = None):
             L.pmf_status_string.restype = ctypes.c_char_p
             L.pmf_version.argtypes = []
             L.pmf_version.restype = ctypes.c_char_p
+            L.pmf_solve_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32p, i32, vp,
+                                            ctypes.POINTER(ctypes.c_int64), vp]
             L.pmf_last_error.argtypes = []
             L.pmf_last_error.restype = ctypes.c_char_p
             for name in EXPORTS:
