@@ -53,13 +53,20 @@ def _first_instances(wl, n):
     return wl
 
 
+def mode_name(segments: int, m: int) -> str:
+    return "m2" if segments == 1 else ("m1" if segments == m else f"seg{segments}")
+
+
+MODE_TEXT = {"m2": "lambda-sequential GGT warm start (one instance per seed)",
+             "m1": "lambda-concurrent (one cold instance per seed x lambda)"}
+
+
 def describe(wl, mode):
     ims = sorted({f"{wl.images[i.image].W}x{wl.images[i.image].H}" for i in wl.instances})
+    text = MODE_TEXT.get(mode, f"each seed's schedule in {mode[3:]} warm-started pieces" if mode.startswith("seg") else mode)
     return {"workload": wl.name, "images": len(wl.images), "image_sizes": ims,
             "instances": len(wl.instances), "lambdas_per_instance": int(len(wl.instances[0].lambdas)),
-            "solves": wl.n_solves, "pixel_solves": wl.pixel_solves,
-            "mode": {"m2": "lambda-sequential GGT warm start (one instance per seed)",
-                     "m1": "lambda-concurrent (one cold instance per seed x lambda)"}[mode]}
+            "solves": wl.n_solves, "pixel_solves": wl.pixel_solves, "mode": text}
 
 
 # ----------------------------------------------------------------------------
@@ -139,6 +146,30 @@ def quick_rate(wl, dev, tuning, reps=3):
     return float(np.median(ts[1:]))
 
 
+def resolve_mode(args, wl, dev, tuning0):
+    """(segments, knobs, note) for the requested mode.  auto: the autotuner's
+    cached choice for this GPU and workload class, else the fastest of one
+    chain per seed, the middle split and one instance per (seed, lambda)."""
+    from paper_1509_06004_b300 import autotune
+    m = min(len(i.lambdas) for i in wl.instances)
+    if args.mode == "m2":
+        return 1, tuning0, None
+    if args.mode == "m1":
+        return m, tuning0, None
+    if args.mode.startswith("seg"):
+        return int(args.mode[3:]), tuning0, None
+    c = autotune.cached(wl, dev.index)
+    if c is not None and not tuning0:
+        knobs = {k: c[k] for k in autotune.DEFAULTS}
+        return int(c["segments"]), knobs, {"source": "autotune cache", "class": autotune.workload_class(wl),
+                                           "tuned_ms": c.get("ms")}
+    divs = autotune.divisors(m)
+    cands = sorted({1, divs[len(divs) // 2], m})
+    probe = {s: quick_rate(wl.split_segments(s) if s > 1 else wl, dev, tuning0) for s in cands}
+    best = min(probe, key=probe.get)
+    return best, tuning0, {"source": "probe", "ms": {mode_name(k, m): v for k, v in probe.items()}}
+
+
 def run_ours(args, rank, world, dev):
     import torch
     from paper_1509_06004_b300 import pmf
@@ -146,23 +177,17 @@ def run_ours(args, rank, world, dev):
     wl = WORKLOADS[args.workload](args.seed + rank)
     tuning0 = {k: v for k, v in (("tile_h", args.tile_h), ("sweeps", args.sweeps),
                                  ("relabel_every", args.relabel_every)) if v}
-    mode_probe = None
-    if args.mode == "auto":
-        # both batching modes give identical outputs; the faster one is timed
-        ms2 = quick_rate(wl, dev, tuning0)
-        ms1 = quick_rate(wl.split_lambdas(), dev, tuning0)
-        args.mode = "m1" if ms1 < ms2 else "m2"
-        mode_probe = {"m2_ms": ms2, "m1_ms": ms1, "chosen": args.mode}
-    if args.mode == "m1":
-        wl = wl.split_lambdas()
-    tuning = {k: v for k, v in (("tile_h", args.tile_h), ("sweeps", args.sweeps),
-                                ("relabel_every", args.relabel_every)) if v}
+    m = min(len(i.lambdas) for i in wl.instances)
+    segments, tuning, mode_probe = resolve_mode(args, wl, dev, tuning0)
+    args.mode = mode_name(segments, m)
+    if segments > 1:
+        wl = wl.split_segments(segments)
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         b = pmf.batch_from_workload(wl, device=dev.index, stream=stream, **tuning)
     lam = np.stack([i.lambdas for i in wl.instances]).astype(np.int32)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    tile_px = 32 * b.tuning()["tile_h"]
+    tile_px = 30 * b.tuning()["tile_h"]     # interior pixels of a tile
 
     def step():
         b.solve(lam, stream=stream)
@@ -225,8 +250,9 @@ def run_ours(args, rank, world, dev):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": dict(describe(wl, args.mode), tile=f"32x{tile_px // 32}",
+        "config": dict(describe(wl, args.mode), tile=f"30x{tile_px // 30} (+2 mirrored columns)",
                        sweeps=b.tuning()["sweeps"], relabel_every_pct=b.tuning()["relabel_every"],
+                       label_slack=b.tuning()["label_slack"],
                        l2="flushed between timed steps (512 MB write)",
                        parallelism=f"replicas x{world} (independent instances, no collective)"),
         "solves_per_s": solves_s,
@@ -240,7 +266,7 @@ def run_ours(args, rank, world, dev):
         "clocks": clk.summary(),
     }
     if mode_probe:
-        out["config"]["mode_probe_ms"] = mode_probe
+        out["config"]["mode_choice"] = mode_probe
     if rank == 0 and not args.no_per_solve:
         out["per_solve_launch"] = per_solve_launch(args, wl, dev, pmf)
         out["per_solve_launch"]["batched_over_per_solve"] = value / world / out["per_solve_launch"]["value"]
@@ -382,10 +408,7 @@ def cpu_baseline(wl, seconds: float):
 # ----------------------------------------------------------------------------
 def run_reference(args, rank, world):
     wl = WORKLOADS[args.workload](args.seed)
-    if args.mode == "m1":
-        wl = wl.split_lambdas()
-    if args.mode == "auto":
-        args.mode = "m2"   # the oracle solves every (seed, lambda) from scratch in both modes
+    args.mode = "m2"   # the oracle solves every (seed, lambda) from scratch whatever the batching
     for _ in range(args.warmup):
         cpu_baseline(wl, min(2.0, args.cpu_seconds / 4))
     vals = []
@@ -411,7 +434,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="supergraph-480x320")
-    ap.add_argument("--mode", choices=["auto", "m2", "m1"], default="auto")
+    ap.add_argument("--mode", default="auto", help="auto | m2 | m1 | seg<N>")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tile-h", type=int, default=0)
     ap.add_argument("--sweeps", type=int, default=0)

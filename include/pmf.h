@@ -89,9 +89,9 @@ typedef struct {
 typedef struct {
     int32_t tile_h;          /* rows per tile, 4 or 8 (tiles are 32 px wide); default 8 */
     int32_t sweeps;          /* push/relabel sweeps per tile visit; default 8 */
-    int32_t relabel_every;   /* global relabel after relabel_every * n_tiles(instance)
-                                push/relabel tile visits, in percent of n_tiles;
-                                default 200 (= 2 visits per tile) */
+    int32_t relabel_every;   /* a push/relabel phase may spend relabel_every% of the
+                                tiles it starts with in tile visits before the next
+                                global relabel; default 800 (8 visits per tile) */
     int32_t max_visits_per_tile; /* watchdog: an instance stops with
                                 PMF_ERR_NOT_CONVERGED after this many visits per
                                 tile per lambda step on average; default 2000 */
@@ -104,7 +104,10 @@ typedef struct {
     int32_t trace;           /* 1 = record instance phase changes (pmf_get_trace) */
     int32_t poll_ns;         /* longest sleep of an idle worker warp between polls of
                                 its queue slot, ns; default 256 */
-    int32_t reserved[3];
+    int32_t label_slack;     /* labels more than this above the largest finite distance
+                                of the last global relabel are parked until the next
+                                relabel; default 16 (0 = default, -1 = off) */
+    int32_t reserved[2];
 } pmf_tuning;
 
 /* One instance phase change recorded on the device (tuning.trace = 1). */

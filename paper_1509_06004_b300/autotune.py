@@ -1,0 +1,169 @@
+"""Autotuner: batching mode and solver knobs for a class of workloads.
+
+The solve's speed depends on how a seed's lambda schedule is spread over
+instances and on the kernel knobs, and the best choice shifts with image size,
+instance count and schedule length:
+
+* ``segments`` — each seed's schedule is cut into this many consecutive
+  pieces, each its own warm-started instance (1 = one lambda-sequential chain
+  per seed; schedule length = every (seed, lambda) cold, the paper's
+  lambda-supergraph); more pieces give the GPU more independent work, fewer
+  keep more warm-start reuse;
+* ``tile_h`` (rows per tile), ``sweeps`` (push/relabel sweeps per tile visit),
+  ``relabel_every`` (visit budget of a push/relabel phase, percent of its
+  tiles) and ``label_slack`` (parking threshold above the last exact distance).
+
+``tune`` times candidates on the GPU by coordinate descent inside a time
+budget; choices are cached in a JSON file keyed by (GPU name, workload class).
+Results never depend on the choice (outputs are unique), only speed does.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE_PATH = os.path.join(HERE, "tuned.json")
+
+DEFAULTS = {"tile_h": 8, "sweeps": 8, "relabel_every": 800, "label_slack": 16}
+SPACE = {
+    "tile_h": [4, 8],
+    "sweeps": [4, 8, 16],
+    "relabel_every": [400, 800, 1600],
+    "label_slack": [8, 16, 32],
+}
+
+
+def divisors(m: int) -> list[int]:
+    return [d for d in range(1, m + 1) if m % d == 0]
+
+
+def _bucket(v: float) -> int:
+    """Power-of-two bucket (as an exponent) of a positive size."""
+    return int(round(math.log2(max(1.0, float(v)))))
+
+
+def workload_class(wl) -> str:
+    """Key of the workload's class: mean image size, instance count and
+    schedule length, each bucketed to a power of two (the lambda count exactly)."""
+    px = np.mean([wl.images[i.image].H * wl.images[i.image].W for i in wl.instances])
+    lens = sorted({len(i.lambdas) for i in wl.instances})
+    return f"px2^{_bucket(px)}-inst2^{_bucket(len(wl.instances))}-lam{'/'.join(map(str, lens))}"
+
+
+def gpu_name(device: int = 0) -> str:
+    import torch
+    return torch.cuda.get_device_name(device)
+
+
+def load_cache(path: str = CACHE_PATH) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str = CACHE_PATH) -> None:
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def cached(wl, device: int = 0, path: str = CACHE_PATH) -> dict | None:
+    return load_cache(path).get(f"{gpu_name(device)}|{workload_class(wl)}")
+
+
+def gpu_measure(wl, segments: int, knobs: dict, reps: int = 2, device: int = 0) -> float:
+    """Median device time (ms) of ``reps`` solves (after one warm-up) of the
+    workload cut into ``segments`` pieces per seed."""
+    import torch
+    from . import pmf
+    w = wl.split_segments(segments) if segments > 1 else wl
+    stream = torch.cuda.Stream(device=device)
+    b = pmf.batch_from_workload(w, device=device, stream=stream, **knobs)
+    lam = np.stack([i.lambdas for i in w.instances]).astype(np.int32)
+    ts = []
+    try:
+        for r in range(reps + 1):
+            b.solve(lam, stream=stream)
+            st = b.sync(check=False)
+            if any(s != pmf.PMF_OK for s in st):
+                return float("inf")
+            if r:
+                ts.append(b.timing()[0])
+    finally:
+        b.close()
+    return float(np.median(ts))
+
+
+def tune(wl, measure=None, budget_s: float = 90.0, reps: int = 2, log=None) -> dict:
+    """Coordinate descent over ``segments`` then each knob of SPACE, starting
+    from DEFAULTS; stops when a full pass brings no gain or the time budget is
+    spent.  ``measure(wl, segments, knobs) -> ms`` defaults to gpu_measure.
+    Returns {"segments", knobs..., "ms"}."""
+    measure = measure or (lambda w, s, k: gpu_measure(w, s, k, reps=reps))
+    m = min(len(i.lambdas) for i in wl.instances)
+    segs = [d for d in divisors(m)]
+    t_end = time.monotonic() + budget_s
+    seen: dict = {}
+
+    def cost(s, k):
+        key = (s, tuple(sorted(k.items())))
+        if key not in seen:
+            seen[key] = measure(wl, s, dict(k))
+            if log:
+                log(f"segments={s} {k} -> {seen[key]:.2f} ms")
+        return seen[key]
+
+    best_s, best_k = 1, dict(DEFAULTS)
+    best = cost(best_s, best_k)
+    improved = True
+    while improved and time.monotonic() < t_end:
+        improved = False
+        for s in segs:
+            if time.monotonic() >= t_end:
+                break
+            c = cost(s, best_k)
+            if c < best:
+                best, best_s, improved = c, s, True
+        for name, vals in SPACE.items():
+            for v in vals:
+                if time.monotonic() >= t_end:
+                    break
+                k = dict(best_k)
+                k[name] = v
+                c = cost(best_s, k)
+                if c < best:
+                    best, best_k, improved = c, k, True
+    out = {"segments": best_s, **best_k, "ms": best}
+    return out
+
+
+def tune_and_cache(wl, device: int = 0, budget_s: float = 90.0, path: str = CACHE_PATH, log=None) -> dict:
+    res = tune(wl, measure=lambda w, s, k: gpu_measure(w, s, k, device=device), budget_s=budget_s, log=log)
+    cache = load_cache(path)
+    res["class"] = workload_class(wl)
+    cache[f"{gpu_name(device)}|{workload_class(wl)}"] = res
+    save_cache(cache, path)
+    return res
+
+
+if __name__ == "__main__":
+    import argparse
+    import sys
+    sys.path.insert(0, os.path.dirname(HERE))
+    from paper_1509_06004_b300 import inputs
+    ap = argparse.ArgumentParser(description="tune and cache the solver settings for a workload")
+    ap.add_argument("--workload", default="supergraph-480x320",
+                    choices=["supergraph-480x320", "parametric-320x240", "uneven-64", "single-64x64"])
+    ap.add_argument("--budget", type=float, default=90.0)
+    a = ap.parse_args()
+    wl = {"supergraph-480x320": inputs.supergraph_480x320, "parametric-320x240": inputs.parametric_320x240,
+          "uneven-64": inputs.uneven_batch, "single-64x64": inputs.single_maxflow_64}[a.workload]()
+    print(json.dumps(tune_and_cache(wl, budget_s=a.budget, log=lambda s: print(s, flush=True))))

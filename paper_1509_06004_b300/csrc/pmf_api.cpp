@@ -154,12 +154,14 @@ pmf_status cuda_err_at(cudaError_t e, const char *where) {
 void apply_defaults(pmf_tuning *t) {
     if (t->tile_h != 4 && t->tile_h != 8) t->tile_h = 8;
     if (t->sweeps <= 0) t->sweeps = 8;
-    if (t->relabel_every <= 0) t->relabel_every = 200;
+    if (t->relabel_every <= 0) t->relabel_every = 800;
     if (t->max_visits_per_tile <= 0) t->max_visits_per_tile = 2000;
     if (t->mode != 1) t->mode = 0;
     if (t->use_graph != 0) t->use_graph = 1;
     t->trace = t->trace ? 1 : 0;
     if (t->poll_ns <= 0) t->poll_ns = 256;
+    if (t->label_slack == 0) t->label_slack = 16;
+    if (t->label_slack < 0) t->label_slack = -1;
 }
 
 // per-instance tile geometry for the current tile height; uploads the table
@@ -446,6 +448,7 @@ pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_la
     b->P.trace = b->tune.trace ? (TraceEvent *)(b->ws + b->L.trace) : nullptr;
     b->P.sweeps = b->tune.sweeps;
     b->P.poll_ns = b->tune.poll_ns;
+    b->P.label_slack = b->tune.label_slack < 0 ? 0 : b->tune.label_slack;
     b->P.relabel_pct = b->tune.relabel_every;
     b->P.max_visits_per_tile = b->tune.max_visits_per_tile;
     const bool geo_changed = (b->P.tile_h != b->tune.tile_h) || (b->last_n_lambda != n_lambda);

@@ -44,7 +44,10 @@ struct InstState {               // mutable during a solve
     // written only by the warp that runs a phase change (nothing of the
     // instance is queued or running then); read by the workers
     int32_t phase, k, epoch, status;
-    int32_t vflags, pad0_, pad1_, pad2_;
+    int32_t vflags;
+    int32_t pr_budget;               // push/relabel visits allowed before the next global relabel
+    int32_t dmax;                    // largest finite distance found by the current relabel
+    int32_t lab_cap;                 // labels at or above this are treated as "cannot reach t"
     unsigned long long pr_mark;      // pr_visits when the current push/relabel phase began
     unsigned long long step_mark;    // pr_visits + bfs_visits when the current lambda step began
     unsigned long long epochs;       // global relabels so far
@@ -102,7 +105,7 @@ struct Params {
     unsigned long long ring_mask;
     int32_t n_inst, n_tiles_total, max_lambdas, sweeps;
     int32_t relabel_pct, tile_h;
-    int32_t poll_ns, pad_p_;
+    int32_t poll_ns, label_slack;
     long long max_visits_per_tile;
     long long stall_ns;          // a worker gives up after this long without progress
     long long max_ns;            // ... or after this long in one launch

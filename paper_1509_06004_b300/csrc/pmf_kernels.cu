@@ -173,8 +173,9 @@ __device__ __forceinline__ DevInst load_inst(const Params &P, int inst) {
 // instance phase changes, run by the warp that finished the instance's last
 // outstanding item (so nothing of this instance is queued or running)
 // --------------------------------------------------------------------------
-__device__ void enqueue_tiles(const Params &P, int inst, const DevInst &D, bool only_active) {
+__device__ int enqueue_tiles(const Params &P, int inst, const DevInst &D, bool only_active) {
     const int lane = threadIdx.x & 31;
+    int total = 0;
     for (int c0 = 0; c0 < D.n_tiles; c0 += 32) {
         const int t = D.tile_base + c0 + lane;
         bool sel = (c0 + lane) < D.n_tiles;
@@ -182,6 +183,7 @@ __device__ void enqueue_tiles(const Params &P, int inst, const DevInst &D, bool 
         const unsigned m = __ballot_sync(FULL_MASK, sel);
         const int cnt = __popc(m);
         if (cnt == 0) continue;
+        total += cnt;
         if (sel) P.tiles[t].state = T_QUEUED;
         unsigned long long base = 0;
         if (lane == 0) {
@@ -198,6 +200,7 @@ __device__ void enqueue_tiles(const Params &P, int inst, const DevInst &D, bool 
             if (slot_wait(P, slot, true, &dummy)) *slot = t;
         }
     }
+    return total;
 }
 
 __device__ void trace(const Params &P, int inst, int event, volatile InstState *S) {
@@ -227,6 +230,7 @@ __device__ void transition(const Params &P, int inst) {
             S->phase = PH_DONE;
             atomicAdd(&P.g->inst_done, 1);
         } else if (phase == PH_PR) {           // start a global relabel
+            S->dmax = 0;
             S->epoch = S->epoch + 1;
             S->epochs = S->epochs + 1;
             S->phase = PH_BFS;
@@ -267,7 +271,22 @@ __device__ void transition(const Params &P, int inst) {
         __threadfence();
     }
     mode = __shfl_sync(FULL_MASK, mode, 0);
-    if (mode) enqueue_tiles(P, inst, D, mode == 2);
+    if (mode) {
+        const int n = enqueue_tiles(P, inst, D, mode == 2);
+        // a push/relabel phase may spend relabel_pct% of the tiles it starts
+        // with (at least 4 visits) before the next global relabel: when only
+        // a few tiles hold active pixels, stranded excess is otherwise pushed
+        // back and forth between them long before a relabel removes it
+        if (lane == 0 && S->phase == PH_PR) {
+            const long long bud = (long long)P.relabel_pct * n / 100;
+            S->pr_budget = (int)(bud < 4 ? 4 : bud);
+            // labels far above every exact distance of the last relabel belong
+            // to excess that keeps climbing without reaching t: park it until
+            // the next relabel (which re-activates whatever can still reach t)
+            const long long cap = (long long)S->dmax + P.label_slack;
+            S->lab_cap = (P.label_slack <= 0 || cap >= D.hcap) ? D.hcap : (int)cap;
+        }
+    }
 }
 
 // finish an item: wake neighbours, requeue or retire the tile, maybe change
@@ -451,7 +470,7 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
     __syncwarp();
 
     int outU = 0, outD = 0;
-    const int hcap = D.hcap;
+    const int hcap = min(D.hcap, *(volatile int *)&P.ist[inst].lab_cap);
     unsigned nsw = 0;
     bool any_act;
     {
@@ -614,7 +633,7 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
         if (df) atomicAdd(&P.ist[inst].flow, (unsigned long long)df);
         const unsigned long long v = atomicAdd(&P.ist[inst].pr_visits, 1ULL) + 1;
         const long long since = (long long)(v - *(volatile unsigned long long *)&P.ist[inst].pr_mark);
-        if (since * 100 >= (long long)P.relabel_pct * D.n_tiles) P.ist[inst].want_bfs = 1;
+        if (since >= (long long)*(volatile int *)&P.ist[inst].pr_budget) P.ist[inst].want_bfs = 1;
     }
 }
 
@@ -776,9 +795,15 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
         }
         cnt += __popc(__ballot_sync(FULL_MASK, ((epos >> i) & 1u) && d[i] < HINF));
     }
+    int dm = 0;
+#pragma unroll
+    for (int i = 0; i < TH; ++i) dm = (own && d[i] < HINF) ? max(dm, d[i]) : dm;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dm = max(dm, __shfl_down_sync(FULL_MASK, dm, o));
     __threadfence();
     __syncwarp();
     if (lane == 0) {
+        if (dm > 0) atomicMax(&P.ist[inst].dmax, dm);
         *(volatile int *)&TS->epoch = epoch;
         const int old = TS->active;
         TS->active = cnt;
@@ -915,8 +940,11 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
         s.epoch = 1;
         s.vflags = P.inst_flags[i] | P.img_flags[D.image];
         s.status = flags_to_status(s.vflags);
-        s.pad0_ = s.pad1_ = s.pad2_ = s.pad3_ = 0;
+        s.pad3_ = 0;
         s.pr_mark = 0;
+        s.pr_budget = D.n_tiles;
+        s.dmax = 0;
+        s.lab_cap = D.hcap;
         s.step_mark = 0;
         s.epochs = 1;
         s.outstanding = D.n_tiles;

@@ -172,6 +172,21 @@ class Workload:
         return sum(self.images[i.image].H * self.images[i.image].W * len(i.lambdas)
                    for i in self.instances)
 
+    def split_segments(self, segments: int) -> "Workload":
+        """Every instance's schedule cut into ``segments`` consecutive pieces of
+        equal length, each its own instance (warm-started inside a piece, cold
+        at its first lambda).  segments = 1 is the workload itself; segments =
+        schedule length is split_lambdas()."""
+        out = Workload(self.name + (f"/seg{segments}" if segments > 1 else ""), list(self.images), [])
+        for inst in self.instances:
+            m = len(inst.lambdas)
+            if m % segments:
+                raise ValueError(f"{segments} segments do not divide a schedule of {m}")
+            for part in np.split(inst.lambdas, segments):
+                out.instances.append(Instance(inst.image, inst.src0, inst.slope, inst.sink,
+                                              part.astype(np.int32), inst.seed_origin))
+        return out
+
     def split_lambdas(self) -> "Workload":
         """The same solves with every (instance, lambda) as its own one-lambda
         instance (the lambda-concurrent form: no warm start between lambdas)."""

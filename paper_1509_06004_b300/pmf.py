@@ -66,7 +66,8 @@ class Tuning(ctypes.Structure):
                 ("relabel_every", ctypes.c_int32), ("max_visits_per_tile", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("trace", ctypes.c_int32),
-                ("poll_ns", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("poll_ns", ctypes.c_int32), ("label_slack", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class TraceEvent(ctypes.Structure):
