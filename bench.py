@@ -130,6 +130,23 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over all ranks (the job's time is the slowest
+    rank's); the only collective the benchmark uses."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Each rank solves its own replica of the workload, drawn with its own seed
+    (instances are independent: weak scaling, no data exchange)."""
+    return seed + rank
+
+
 def quick_rate(wl, dev, tuning, reps=3):
     """Median device time (ms) of a few solves of a workload (mode choice)."""
     import torch
@@ -174,7 +191,7 @@ def run_ours(args, rank, world, dev):
     import torch
     from paper_1509_06004_b300 import pmf
 
-    wl = WORKLOADS[args.workload](args.seed + rank)
+    wl = WORKLOADS[args.workload](rank_seed(args.seed, rank))
     tuning0 = {k: v for k, v in (("tile_h", args.tile_h), ("sweeps", args.sweeps),
                                  ("relabel_every", args.relabel_every)) if v}
     m = min(len(i.lambdas) for i in wl.instances)
@@ -226,11 +243,7 @@ def run_ours(args, rank, world, dev):
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(c) for a, c in zip(ev0, ev1)]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
     pix = wl.pixel_solves
     value = world * pix * args.steps / total_s
     solves_s = world * wl.n_solves * args.steps / total_s
@@ -273,6 +286,8 @@ def run_ours(args, rank, world, dev):
     if not args.no_e2e:
         out["e2e"] = e2e(args, wl, b, lam, dev, stream, pmf, world)
     b.close()
+    if rank == 0 and args.serving_requests > 0:
+        out["serving"] = serving_bench(args, dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     return out
@@ -369,13 +384,28 @@ def e2e(args, wl, b, lam, dev, stream, pmf, world):
     for _ in range(n):
         one()
     torch.cuda.synchronize(dev)
-    dt = (time.perf_counter() - t0) / n
-    if world > 1:
-        t = torch.tensor([dt], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks((time.perf_counter() - t0) / n, world, dev)
     return {"value": world * wl.pixel_solves / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3, "steps": n}
+
+
+def serving_bench(args, dev):
+    """Poisson request stream (one image of random size, its seeds and lambda
+    schedule per request) served with continuous batching, against serving
+    the same stream one request at a time on the whole GPU."""
+    import torch
+    from paper_1509_06004_b300 import serving
+    reqs = inputs.serving_stream(args.serving_rate, args.serving_requests, seed=0, max_side=args.serving_max_side)
+    warm = inputs.serving_stream(args.serving_rate, 3, seed=99, max_side=args.serving_max_side)
+    out = {"rate_per_s": args.serving_rate, "requests": len(reqs), "max_side": args.serving_max_side,
+           "budget_bytes": args.serving_budget, "pixel_solves": sum(r.workload.pixel_solves for r in reqs)}
+    for name, slots in (("continuous", args.serving_slots), ("one_at_a_time", 1)):
+        serving.serve(warm, slots=slots, budget_bytes=args.serving_budget, device=dev.index, segments=5)
+        st = serving.serve(reqs, slots=slots, budget_bytes=args.serving_budget, device=dev.index, segments=5)
+        out[name] = st.summary()
+        out[name]["slots"] = slots
+        torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(wl, seconds: float):
@@ -444,6 +474,11 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-per-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=40, help="0 = skip the serving run")
+    ap.add_argument("--serving-rate", type=float, default=50.0)
+    ap.add_argument("--serving-max-side", type=int, default=800)
+    ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-budget", type=int, default=64 << 30)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

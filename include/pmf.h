@@ -107,7 +107,9 @@ typedef struct {
     int32_t label_slack;     /* labels more than this above the largest finite distance
                                 of the last global relabel are parked until the next
                                 relabel; default 16 (0 = default, -1 = off) */
-    int32_t reserved[2];
+    int32_t grid_blocks;     /* persistent grid size in blocks (overrides blocks_per_sm;
+                                0 = auto); lets several batches share the GPU */
+    int32_t reserved;
 } pmf_tuning;
 
 /* One instance phase change recorded on the device (tuning.trace = 1). */

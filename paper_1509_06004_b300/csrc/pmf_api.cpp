@@ -8,7 +8,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -96,6 +98,72 @@ Layout make_layout(const pmf_batch_desc *d) {
     return L;
 }
 
+// Pinned host memory for the batches' small result mirrors comes from one
+// process-wide arena: page-locked allocation and release synchronise the whole
+// device, so a batch created or destroyed while others run on the GPU must not
+// call cudaHostAlloc / cudaFreeHost.  Chunks are allocated once and reused.
+class PinnedArena {
+public:
+    void *alloc(size_t n) {
+        n = align_up(n);
+        std::lock_guard<std::mutex> g(mu_);
+        for (Chunk &c : chunks_) {
+            for (size_t i = 0; i < c.free.size(); ++i) {
+                if (c.free[i].second >= n) {
+                    char *p = c.base + c.free[i].first;
+                    c.free[i].first += n;
+                    c.free[i].second -= n;
+                    if (c.free[i].second == 0) c.free.erase(c.free.begin() + (long)i);
+                    return p;
+                }
+            }
+        }
+        const size_t sz = std::max<size_t>(n, (size_t)16 << 20);
+        void *base = nullptr;
+        if (cudaHostAlloc(&base, sz, cudaHostAllocPortable) != cudaSuccess) return nullptr;
+        chunks_.push_back(Chunk{(char *)base, sz, {{n, sz - n}}});
+        if (chunks_.back().free.back().second == 0) chunks_.back().free.pop_back();
+        return base;
+    }
+    void release(void *p, size_t n) {
+        if (!p) return;
+        n = align_up(n);
+        std::lock_guard<std::mutex> g(mu_);
+        for (Chunk &c : chunks_) {
+            char *q = (char *)p;
+            if (q < c.base || q >= c.base + c.size) continue;
+            const size_t off = (size_t)(q - c.base);
+            auto it = c.free.begin();
+            while (it != c.free.end() && it->first < off) ++it;
+            it = c.free.insert(it, {off, n});
+            // merge with the following and the preceding free block
+            if (it + 1 != c.free.end() && it->first + it->second == (it + 1)->first) {
+                it->second += (it + 1)->second;
+                c.free.erase(it + 1);
+            }
+            if (it != c.free.begin() && (it - 1)->first + (it - 1)->second == it->first) {
+                (it - 1)->second += it->second;
+                c.free.erase(it);
+            }
+            return;
+        }
+    }
+
+private:
+    struct Chunk {
+        char *base;
+        size_t size;
+        std::vector<std::pair<size_t, size_t>> free;   // (offset, length), sorted
+    };
+    std::mutex mu_;
+    std::vector<Chunk> chunks_;
+};
+
+PinnedArena &pinned_arena() {
+    static PinnedArena *a = new PinnedArena();   // lives until exit (chunks are never returned)
+    return *a;
+}
+
 struct DeviceGuard {
     int old = -1;
     explicit DeviceGuard(int dev) {
@@ -134,6 +202,7 @@ struct pmf_batch {
     long long *flows_h = nullptr;
     Globals *glob_h = nullptr;
     DevInst *dinst_h = nullptr;
+    size_t pinned_bytes[5] = {0, 0, 0, 0, 0};
     // captured graph
     cudaGraphExec_t gexec = nullptr;
     bool graph_valid = false;
@@ -194,6 +263,7 @@ pmf_status refresh_geometry(pmf_batch *b, cudaStream_t s) {
 }
 
 int grid_size(pmf_batch *b) {
+    if (b->tune.grid_blocks > 0) return b->tune.grid_blocks;
     int bps = b->tune.blocks_per_sm;
     if (bps <= 0) {
         if (worker_occupancy(b->tune.tile_h, &bps) != cudaSuccess || bps <= 0) bps = 4;
@@ -283,11 +353,17 @@ pmf_status pmf_create_batch(const pmf_batch_desc *desc, void *dev_workspace, siz
     apply_defaults(&b->tune);
     cudaError_t e = cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
     const size_t nl = (size_t)desc->n_inst * desc->max_lambdas;
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->lam_h, sizeof(int32_t) * nl, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->ist_h, sizeof(InstState) * desc->n_inst, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->flows_h, sizeof(long long) * nl, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->glob_h, sizeof(Globals), cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->dinst_h, sizeof(DevInst) * desc->n_inst, cudaHostAllocDefault);
+    b->pinned_bytes[0] = sizeof(int32_t) * nl;
+    b->pinned_bytes[1] = sizeof(InstState) * desc->n_inst;
+    b->pinned_bytes[2] = sizeof(long long) * nl;
+    b->pinned_bytes[3] = sizeof(Globals);
+    b->pinned_bytes[4] = sizeof(DevInst) * desc->n_inst;
+    void **dst[5] = {(void **)&b->lam_h, (void **)&b->ist_h, (void **)&b->flows_h, (void **)&b->glob_h,
+                     (void **)&b->dinst_h};
+    for (int j = 0; j < 5 && e == cudaSuccess; ++j) {
+        *dst[j] = pinned_arena().alloc(b->pinned_bytes[j]);
+        if (!*dst[j]) e = cudaErrorMemoryAllocation;
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev_t0);
@@ -343,7 +419,8 @@ pmf_status pmf_create_batch(const pmf_batch_desc *desc, void *dev_workspace, siz
 pmf_status pmf_set_tuning(pmf_batch *b, const pmf_tuning *t) {
     if (!b || !t) return PMF_ERR_INVALID_ARG;
     if (t->tile_h != 0 && t->tile_h != 4 && t->tile_h != 8) return PMF_ERR_INVALID_ARG;
-    if (t->sweeps < 0 || t->relabel_every < 0 || t->max_visits_per_tile < 0 || t->blocks_per_sm < 0)
+    if (t->sweeps < 0 || t->relabel_every < 0 || t->max_visits_per_tile < 0 || t->blocks_per_sm < 0 ||
+        t->grid_blocks < 0)
         return PMF_ERR_INVALID_ARG;
     if (b->in_flight) {
         DeviceGuard dg(b->device);
@@ -660,11 +737,11 @@ void pmf_destroy_batch(pmf_batch *b) {
     for (cudaEvent_t ev : {b->ev_t0, b->ev_w0, b->ev_w1, b->ev_t1})
         if (ev) cudaEventDestroy(ev);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    if (b->lam_h) cudaFreeHost(b->lam_h);
-    if (b->ist_h) cudaFreeHost(b->ist_h);
-    if (b->flows_h) cudaFreeHost(b->flows_h);
-    if (b->glob_h) cudaFreeHost(b->glob_h);
-    if (b->dinst_h) cudaFreeHost(b->dinst_h);
+    pinned_arena().release(b->lam_h, b->pinned_bytes[0]);
+    pinned_arena().release(b->ist_h, b->pinned_bytes[1]);
+    pinned_arena().release(b->flows_h, b->pinned_bytes[2]);
+    pinned_arena().release(b->glob_h, b->pinned_bytes[3]);
+    pinned_arena().release(b->dinst_h, b->pinned_bytes[4]);
     delete b;
 }
 

@@ -173,18 +173,30 @@ __device__ __forceinline__ DevInst load_inst(const Params &P, int inst) {
 // instance phase changes, run by the warp that finished the instance's last
 // outstanding item (so nothing of this instance is queued or running)
 // --------------------------------------------------------------------------
-__device__ int enqueue_tiles(const Params &P, int inst, const DevInst &D, bool only_active) {
+// Queue tiles of an instance for its new phase.  Each tile is claimed with a
+// CAS from IDLE: tiles released from earlier chunks start running at once and
+// may already have woken a neighbour that this loop has not reached yet; that
+// neighbour is queued (or running) and must not be queued twice.
+__device__ int count_active_tiles(const Params &P, const DevInst &D) {
     const int lane = threadIdx.x & 31;
     int total = 0;
+    for (int c0 = 0; c0 < D.n_tiles; c0 += 32) {
+        const bool sel = (c0 + lane) < D.n_tiles && ldv(&P.tiles[D.tile_base + c0 + lane].active) > 0;
+        total += __popc(__ballot_sync(FULL_MASK, sel));
+    }
+    return total;
+}
+
+__device__ void enqueue_tiles(const Params &P, int inst, const DevInst &D, bool only_active) {
+    const int lane = threadIdx.x & 31;
     for (int c0 = 0; c0 < D.n_tiles; c0 += 32) {
         const int t = D.tile_base + c0 + lane;
         bool sel = (c0 + lane) < D.n_tiles;
         if (sel && only_active) sel = ldv(&P.tiles[t].active) > 0;
+        if (sel) sel = atomicCAS(&P.tiles[t].state, T_IDLE, T_QUEUED) == T_IDLE;
         const unsigned m = __ballot_sync(FULL_MASK, sel);
         const int cnt = __popc(m);
         if (cnt == 0) continue;
-        total += cnt;
-        if (sel) P.tiles[t].state = T_QUEUED;
         unsigned long long base = 0;
         if (lane == 0) {
             atomicAdd(&P.ist[inst].outstanding, cnt);
@@ -194,13 +206,13 @@ __device__ int enqueue_tiles(const Params &P, int inst, const DevInst &D, bool o
         base = __shfl_sync(FULL_MASK, base, 0);
         __syncwarp();
         if (sel) {
+            __threadfence();
             const unsigned long long tk = base + __popc(m & ((1u << lane) - 1u));
             volatile int *slot = (volatile int *)(P.ring + (tk & P.ring_mask));
             int dummy;
             if (slot_wait(P, slot, true, &dummy)) *slot = t;
         }
     }
-    return total;
 }
 
 __device__ void trace(const Params &P, int inst, int event, volatile InstState *S) {
@@ -271,22 +283,25 @@ __device__ void transition(const Params &P, int inst) {
         __threadfence();
     }
     mode = __shfl_sync(FULL_MASK, mode, 0);
-    if (mode) {
-        const int n = enqueue_tiles(P, inst, D, mode == 2);
+    if (!mode) return;
+    // the phase's parameters are published before any of its tiles can run
+    const int n = (mode == 2) ? count_active_tiles(P, D) : D.n_tiles;
+    if (lane == 0 && S->phase == PH_PR) {
         // a push/relabel phase may spend relabel_pct% of the tiles it starts
         // with (at least 4 visits) before the next global relabel: when only
         // a few tiles hold active pixels, stranded excess is otherwise pushed
         // back and forth between them long before a relabel removes it
-        if (lane == 0 && S->phase == PH_PR) {
-            const long long bud = (long long)P.relabel_pct * n / 100;
-            S->pr_budget = (int)(bud < 4 ? 4 : bud);
-            // labels far above every exact distance of the last relabel belong
-            // to excess that keeps climbing without reaching t: park it until
-            // the next relabel (which re-activates whatever can still reach t)
-            const long long cap = (long long)S->dmax + P.label_slack;
-            S->lab_cap = (P.label_slack <= 0 || cap >= D.hcap) ? D.hcap : (int)cap;
-        }
+        const long long bud = (long long)P.relabel_pct * n / 100;
+        S->pr_budget = (int)(bud < 4 ? 4 : bud);
+        // labels far above every exact distance of the last relabel belong
+        // to excess that keeps climbing without reaching t: park it until
+        // the next relabel (which re-activates whatever can still reach t)
+        const long long cap = (long long)S->dmax + P.label_slack;
+        S->lab_cap = (P.label_slack <= 0 || cap >= D.hcap) ? D.hcap : (int)cap;
     }
+    __threadfence();
+    __syncwarp();
+    enqueue_tiles(P, inst, D, mode == 2);
 }
 
 // finish an item: wake neighbours, requeue or retire the tile, maybe change
@@ -805,7 +820,9 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     if (lane == 0) {
         if (dm > 0) atomicMax(&P.ist[inst].dmax, dm);
         *(volatile int *)&TS->epoch = epoch;
-        const int old = TS->active;
+        // the previous count may have been written from another SM: read it
+        // past L1 (a stale L1 line would corrupt the instance's active total)
+        const int old = ldv(&TS->active);
         TS->active = cnt;
         if (cnt != old) atomicAdd(&P.ist[inst].active, cnt - old);
         atomicAdd(&P.ist[inst].bfs_visits, 1ULL);

@@ -67,7 +67,7 @@ class Tuning(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("trace", ctypes.c_int32),
                 ("poll_ns", ctypes.c_int32), ("label_slack", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("grid_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class TraceEvent(ctypes.Structure):
@@ -354,13 +354,14 @@ class Batch:
 
 
 def batch_from_workload(wl, device: int = 0, stream=None, device_inputs: bool = False,
-                        **tuning) -> Batch:
+                        workspace=None, **tuning) -> Batch:
     """A Batch holding every image and instance of an inputs.Workload, with all
-    capacities uploaded (host path, or device path if device_inputs)."""
+    capacities uploaded (host path, or device path if device_inputs); the
+    workspace is allocated unless a uint8 CUDA tensor of enough bytes is given."""
     import torch
     max_l = max(len(i.lambdas) for i in wl.instances)
     b = Batch([(im.H, im.W) for im in wl.images], [i.image for i in wl.instances], max_l,
-              device=device, stream=stream)
+              device=device, stream=stream, workspace=workspace)
     if tuning:
         b.set_tuning(**tuning)
     conv = (lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).to(f"cuda:{device}")) \

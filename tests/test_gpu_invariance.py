@@ -71,7 +71,8 @@ def test_alone_equals_in_mixed_batch(P):
 
 @pytest.mark.parametrize("knobs", [dict(tile_h=4), dict(sweeps=1), dict(sweeps=32), dict(relabel_every=50),
                                    dict(relabel_every=5000), dict(label_slack=-1), dict(label_slack=1),
-                                   dict(blocks_per_sm=1), dict(poll_ns=8192)])
+                                   dict(blocks_per_sm=1), dict(poll_ns=8192), dict(grid_blocks=1),
+                                   dict(grid_blocks=3), dict(grid_blocks=37), dict(grid_blocks=197, tile_h=4)])
 def test_launch_configuration_does_not_change_results(P, knobs):
     wl = _synthetic(3, 70, 96, 3, 8)
     _same(_solve(P, wl), _solve(P, wl, **knobs))
@@ -286,3 +287,38 @@ def test_trace_and_profile(P):
     sm, wm = b.timing()
     assert sm >= wm > 0
     b.close()
+
+
+def test_concurrent_batches_on_separate_streams(P):
+    """Several batches solving at once on their own streams (as the serving
+    loop runs them) give each batch's results unchanged."""
+    import torch
+    wls = [_synthetic(20 + j, 90 + 7 * j, 120 - 5 * j, 3, 6) for j in range(4)]
+    ref = [_solve(P, w) for w in wls]
+    for grid in (148, 37):
+        streams = [torch.cuda.Stream() for _ in wls]
+        bs = []
+        for w, s in zip(wls, streams):
+            with torch.cuda.stream(s):
+                b = P.batch_from_workload(w, stream=s, grid_blocks=grid, tile_h=4)
+            bs.append(b)
+        for w, s, b in zip(wls, streams, bs):
+            b.solve(np.stack([i.lambdas for i in w.instances]), stream=s)
+        for w, b, r in zip(wls, bs, ref):
+            assert all(x == P.PMF_OK for x in b.sync(check=False))
+            _same(r, [(b.flows(i), b.cuts(i)) for i in range(len(w.instances))])
+            b.close()
+
+
+def test_race_repeated_small_grids(P):
+    """Many repetitions under few workers (the interleavings change from run
+    to run): flows must equal the oracle's every time.  This caught a tile
+    being queued twice while a phase change was still releasing tiles."""
+    wl = _synthetic(3, 70, 96, 3, 8)
+    ref = oracle.solve_workload(wl)
+    for rep in range(12):
+        for grid in (1, 2, 5):
+            res = _solve(P, wl, grid_blocks=grid, tile_h=4 if rep % 2 else 8)
+            for (f, m), (of, om) in zip(res, ref):
+                assert np.array_equal(f, of), (rep, grid)
+                assert np.array_equal(m, om), (rep, grid)

@@ -1,0 +1,113 @@
+"""Serving: admission logic on the CPU (fake backend, virtual clock) and, on
+the GPU, continuous batching whose per-request results equal the results of
+solving each request alone."""
+import numpy as np
+import pytest
+
+from paper_1509_06004_b300 import inputs, serving
+
+
+class FakeBackend:
+    """Requests take a fixed virtual duration; memory is a byte counter."""
+
+    def __init__(self, clock, budget, dur=0.1):
+        self.clock, self.budget, self.dur = clock, budget, dur
+        self.used = 0
+
+    def bytes(self, req):
+        return req.nbytes
+
+    def reserve(self, req):
+        if self.used + req.nbytes > self.budget:
+            return None
+        self.used += req.nbytes
+        return req.nbytes
+
+    def release(self, tok):
+        self.used -= tok
+
+    def in_use(self):
+        return self.used
+
+    def start(self, req, slot, tok):
+        return self.clock.t + self.dur
+
+    def done(self, h):
+        return self.clock.t >= h
+
+    def finish(self, h, collect):
+        return None, None
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 1e-4)
+
+
+class Req:
+    def __init__(self, t, nbytes, px=100):
+        self.arrival_s, self.nbytes = t, nbytes
+        self.workload = type("W", (), {"pixel_solves": px})()
+
+
+def test_scheduler_slots_budget_and_fifo():
+    clk = Clock()
+    be = FakeBackend(clk, budget=100)
+    reqs = [Req(0.00, 40), Req(0.01, 40), Req(0.02, 40), Req(0.03, 10), Req(0.5, 90)]
+    st = serving.Scheduler(be, slots=3, budget_bytes=100).run(reqs, clock=clk, sleep=clk.sleep)
+    c = {x.index: x for x in st.completed}
+    assert len(c) == 5
+    assert st.peak_bytes <= 100 and st.max_concurrent <= 3
+    # the third 40-byte request waits for memory; request 3 (10 bytes) waits behind it (FCFS)
+    assert c[2].admit_s >= c[0].done_s - 1e-9
+    assert c[3].admit_s >= c[2].admit_s
+    # a request arriving while others run is admitted as soon as they free memory
+    assert c[4].admit_s >= 0.5
+    assert all(x.latency_s >= 0.1 - 1e-9 for x in st.completed)
+
+
+def test_scheduler_rejects_oversized_request():
+    clk = Clock()
+    with pytest.raises(ValueError):
+        serving.Scheduler(FakeBackend(clk, 50), 2, 50).run([Req(0.0, 60)], clock=clk, sleep=clk.sleep)
+
+
+def test_device_arena_first_fit_and_merge():
+    a = serving.DeviceArena(4096)
+    x = a.alloc(1000)
+    y = a.alloc(1000)
+    z = a.alloc(1000)
+    assert x[0] == 0 and y[0] == 1024 and z[0] == 2048
+    assert a.alloc(2000) is None
+    a.release(y)
+    a.release(x)
+    assert a.free[0] == (0, 2048)
+    a.release(z)
+    assert a.free == [(0, 4096)] and a.in_use == 0
+
+
+@pytest.mark.gpu
+def test_continuous_batching_equals_alone():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_06004_b300 import build, pmf
+    build.build()
+    reqs = inputs.serving_stream(rate_per_s=1000.0, n_requests=8, seed=3, max_side=256)
+    for r in reqs:       # keep the test short: 4 seeds, 6 lambdas
+        r.workload.instances = r.workload.instances[:4]
+        for inst in r.workload.instances:
+            inst.lambdas = inst.lambdas[:6]
+    st = serving.serve(reqs, slots=3, budget_bytes=1 << 30, realtime=True, collect=True, segments=2)
+    assert st.max_concurrent >= 2
+    for c, r in zip(st.completed, reqs):
+        status, alone = pmf.solve_workload(r.workload)
+        assert all(s == pmf.PMF_OK for s in status)
+        for (fa, ma), f, m in zip(alone, c.flows, c.masks):
+            assert np.array_equal(fa, f) and np.array_equal(ma, m)
