@@ -958,6 +958,7 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
         s.vflags = P.inst_flags[i] | P.img_flags[D.image];
         s.status = flags_to_status(s.vflags);
         s.pad3_ = 0;
+        s.pad_b_ = s.pad_c_ = 0;
         s.pr_mark = 0;
         s.pr_budget = D.n_tiles;
         s.dmax = 0;
