@@ -236,7 +236,8 @@ void apply_defaults(pmf_tuning *t) {
 // per-instance tile geometry for the current tile height; uploads the table
 pmf_status refresh_geometry(pmf_batch *b, cudaStream_t s) {
     const int th = b->tune.tile_h;
-    int base = 0;
+    const int span = BFS_ROWS / th;
+    int base = 0, lbase = 0;
     for (int i = 0; i < b->desc.n_inst; ++i) {
         const int im = b->inst_image[i];
         DevInst &d = b->dinst[i];
@@ -250,6 +251,9 @@ pmf_status refresh_geometry(pmf_batch *b, cudaStream_t s) {
         d.n_tiles = d.tiles_x * d.tiles_y;
         d.tile_base = base;
         base += d.n_tiles;
+        d.lead_base = lbase;
+        d.n_leads = d.tiles_x * ((d.tiles_y + span - 1) / span);
+        lbase += d.n_leads;
         d.hcap = d.H * d.W + 1;
         d.plane_off = b->L.plane_off[i];
         d.img_off = b->L.img_off[im];
@@ -257,6 +261,7 @@ pmf_status refresh_geometry(pmf_batch *b, cudaStream_t s) {
         b->dinst_h[i] = d;
     }
     b->P.n_tiles_total = base;
+    b->P.n_leads_total = lbase;
     b->P.tile_h = th;
     return cuda_err(cudaMemcpyAsync(b->ws + b->L.dev_inst, b->dinst_h, sizeof(DevInst) * b->desc.n_inst,
                                     cudaMemcpyHostToDevice, s));

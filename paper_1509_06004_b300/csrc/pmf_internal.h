@@ -14,6 +14,7 @@ constexpr int TILE_IN = 30;                // interior columns of a tile: lanes 
                                            // and 31 mirror the neighbouring tiles' columns
 constexpr int ROW_ALIGN = 16;              // rows padded so tile heights 4/8/16 divide them
 constexpr int32_t HINF = 0x3fffffff;       // label of a pixel that cannot reach t
+constexpr int BFS_ROWS = 32;               // rows of a relabel strip (a column of tiles)
 constexpr int N_INST_PLANES = 8;           // e, h, rt, fR, fD, src0, slope, ct
 constexpr int N_IMG_PLANES = 2;            // w_h, w_v
 enum Plane { P_E = 0, P_H = 1, P_RT = 2, P_FR = 3, P_FD = 4, P_SRC0 = 5, P_SLOPE = 6, P_CT = 7 };
@@ -34,11 +35,12 @@ struct DevInst {                 // read-only during a solve
     int32_t tile_base;
     int32_t n_lambda;
     int32_t hcap;                // labels >= hcap become HINF (= H*W)
-    int32_t pad_;
+    int32_t lead_base;           // index of this instance's first relabel strip in the leader list
     int64_t plane_off;           // int32 elements from the instance-plane base
     int64_t img_off;             // int32 elements from the image-plane base
     int64_t mask_off;            // bytes from the mask base
-    int64_t pad2_;               // keeps the size a multiple of 16 bytes
+    int32_t n_leads;             // relabel strips (tiles_x * ceil(tiles_y / strip_span))
+    int32_t pad2_;               // keeps the size a multiple of 16 bytes
 };
 
 // 16-byte aligned: the worker reads the first four fields with one 16-byte
@@ -113,6 +115,7 @@ struct Params {
     int32_t *inst_flags;         // [n_inst] validation flags of set_terminals
     unsigned long long ring_mask;
     int32_t n_inst, n_tiles_total, max_lambdas, sweeps;
+    int32_t n_leads_total, pad_l_;
     int32_t relabel_pct, tile_h;
     int32_t poll_ns, label_slack;
     long long max_visits_per_tile;

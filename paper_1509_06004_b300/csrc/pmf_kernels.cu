@@ -60,8 +60,10 @@ __device__ __forceinline__ long long ldv64s(const long long *p) { return *(const
 // are written back as deltas)
 template <int TH>
 struct WarpSmem {
-    int e0[2][TH];   // excess of lanes 1 and 30 at load
-    int f0[2][TH];   // fR of lane 0 (left border edge) and lane 30 (right border edge)
+    int e0[2][TH];          // excess of lanes 1 and 30 at load
+    int f0[2][TH];          // fR of lane 0 (left border edge) and lane 30 (right border edge)
+    int dl0[2][BFS_ROWS];   // relabel: labels of lanes 1 and 30 at load (a strip's side columns)
+    int d[BFS_ROWS][32];    // relabel: the strip's labels, row i / lane l (each lane its own column)
 };
 
 // --------------------------------------------------------------------------
@@ -187,11 +189,13 @@ __device__ int count_active_tiles(const Params &P, const DevInst &D) {
     return total;
 }
 
-__device__ void enqueue_tiles(const Params &P, int inst, const DevInst &D, bool only_active) {
+__device__ void enqueue_tiles(const Params &P, int inst, const DevInst &D, bool only_active, bool leaders_only) {
     const int lane = threadIdx.x & 31;
+    const int span = BFS_ROWS / P.tile_h;
     for (int c0 = 0; c0 < D.n_tiles; c0 += 32) {
         const int t = D.tile_base + c0 + lane;
         bool sel = (c0 + lane) < D.n_tiles;
+        if (sel && leaders_only) sel = (((c0 + lane) / D.tiles_x) % span) == 0;
         if (sel && only_active) sel = ldv(&P.tiles[t].active) > 0;
         if (sel) sel = atomicCAS(&P.tiles[t].state, T_IDLE, T_QUEUED) == T_IDLE;
         const unsigned m = __ballot_sync(FULL_MASK, sel);
@@ -301,7 +305,8 @@ __device__ void transition(const Params &P, int inst) {
     }
     __threadfence();
     __syncwarp();
-    enqueue_tiles(P, inst, D, mode == 2);
+    // a relabel works on strips (their leader tiles are queued); push/relabel on tiles
+    enqueue_tiles(P, inst, D, mode == 2, S->phase == PH_BFS);
 }
 
 // finish an item: wake neighbours, requeue or retire the tile, maybe change
@@ -322,8 +327,9 @@ __device__ void finish(const Params &P, int g, int inst, int phase, bool requeue
         const int lt = g - D.tile_base;
         const int ty = lt / D.tiles_x, tx = lt - ty * D.tiles_x;
         int t = -1;
-        if (lane == 0 && ty > 0) t = g - D.tiles_x;
-        if (lane == 1 && ty < D.tiles_y - 1) t = g + D.tiles_x;
+        const int vs = (phase == PH_BFS) ? BFS_ROWS / P.tile_h : 1;   // strips in a relabel
+        if (lane == 0 && ty >= vs) t = g - vs * D.tiles_x;
+        if (lane == 1 && ty + vs < D.tiles_y) t = g + vs * D.tiles_x;
         if (lane == 2 && tx > 0) t = g - 1;
         if (lane == 3 && tx < D.tiles_x - 1) t = g + 1;
         if (t >= 0) {
@@ -653,15 +659,20 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
 }
 
 // --------------------------------------------------------------------------
-// global-relabel visit: one tile's share of the BFS from t over reverse
+// global-relabel visit: one strip's share of the BFS from t over reverse
 // residual arcs (exact distances by label-correcting relaxation to a fixpoint;
-// unreachable pixels keep HINF).  It also writes the cut mask of the current
-// lambda (1 = cannot reach t = source side) and the tile's active count.
+// unreachable pixels keep HINF).  A strip is a column of BFS_ROWS / TH tiles
+// (30 x 32 pixels), queued through its top ("leader") tile; each lane keeps the
+// strip column's 32 labels in registers and the residual arcs as bit masks, so
+// one visit carries distances across 32 rows.  It also writes the cut mask of
+// the current lambda (1 = cannot reach t = source side) and each member tile's
+// count of active pixels for the push/relabel phase that may follow.
 // --------------------------------------------------------------------------
 template <int TH>
 __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, const DevInst &D,
                           int epoch, int kcur, bool &self_again, unsigned &nbmask) {
-    (void)S;
+    constexpr int BR = BFS_ROWS;
+    constexpr int SPAN = BR / TH;
     const TileGeo T = tile_geo(g, D, TH);
     const int lane = T.lane;
     const bool own = T.inb && !T.ghost;
@@ -674,122 +685,166 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     const int *WH = P.img + D.img_off;
     const int *WV = WH + PS;
     TileState *TS = P.tiles + g;
+    const int vstride = SPAN * D.tiles_x;
 
-    // labels of a neighbouring tile count only once it has been visited in
+    // labels of a neighbouring strip count only once it has been visited in
     // this relabel epoch (otherwise they are left over from push/relabel)
     const bool own_valid = ldv(&TS->epoch) == epoch;
-    const bool vT = T.ty > 0 && ldv(&P.tiles[g - D.tiles_x].epoch) == epoch;
-    const bool vB = T.ty < D.tiles_y - 1 && ldv(&P.tiles[g + D.tiles_x].epoch) == epoch;
+    const bool vT = T.ty >= SPAN && ldv(&P.tiles[g - vstride].epoch) == epoch;
+    const bool vB = T.ty + SPAN < D.tiles_y && ldv(&P.tiles[g + vstride].epoch) == epoch;
     bool vX = own_valid;
     if (lane == 0) vX = T.tx > 0 && ldv(&P.tiles[g - 1].epoch) == epoch;
     if (lane == 31) vX = T.tx < D.tiles_x - 1 && ldv(&P.tiles[g + 1].epoch) == epoch;
     __threadfence();
 
-    int fr[TH], fd[TH], wh[TH], wv[TH], d[TH], dold[TH];
-    unsigned epos = 0;
-#pragma unroll
-    for (int i = 0; i < TH; ++i) {
-        const size_t idx = (size_t)(T.y0 + i) * pitch + T.X;
-        const bool ep = own && __ldcg(E + idx) > 0;
-        const bool rp = own && __ldcg(RT + idx) > 0;
-        if (ep) epos |= 1u << i;
-        fr[i] = (T.inb && lane != 31) ? __ldcg(FR + idx) : 0;
-        fd[i] = own ? __ldcg(FD + idx) : 0;
-        wh[i] = (T.inb && lane != 31) ? __ldg(WH + idx) : 0;
-        wv[i] = own ? __ldg(WV + idx) : 0;
-        d[i] = (T.inb && vX) ? __ldcg(Hh + idx) : HINF;
-        dold[i] = d[i];
-        if (rp) d[i] = min(d[i], 1);
-    }
-    int hT = HINF, wvT = 0, fdT = 0, hB = HINF;
+    // the row above the strip: residual of the arcs up and down across the border
+    int hT = HINF, res_up0 = 0, res_down_above = 0;
     if (own && T.y0 > 0) {
         const size_t j = (size_t)(T.y0 - 1) * pitch + T.X;
-        wvT = __ldg(WV + j);
-        fdT = __ldcg(FD + j);
+        const int wvT = __ldg(WV + j), fdT = __ldcg(FD + j);
+        res_up0 = wvT + fdT;          // row 0 -> above
+        res_down_above = wvT - fdT;   // above -> row 0
         if (vT) hT = __ldcg(Hh + j);
     }
-    if (own && vB) hB = __ldcg(Hh + (size_t)(T.y0 + TH) * pitch + T.X);
+    const bool below = T.y0 + BR < D.rows;
+    int hB = HINF;
+    if (own && vB && below) hB = __ldcg(Hh + (size_t)(T.y0 + BR) * pitch + T.X);
+
+    // residual arcs as bit masks (bit i = row i): R/L/D/U = from the pixel to
+    // that neighbour; E = positive excess; Q = arc from this column to the one
+    // on its right (read by lane 1 from ghost lane 0); V = arc from the right
+    // neighbour into this column (used by lane 30).  Labels live in this
+    // lane's own column of the warp's shared memory.
+    int(*Dl)[32] = S.d;
+    unsigned bR = 0, bL = 0, bD = 0, bU = 0, bE = 0, bQ = 0, bV = 0;
+    int prev_up = res_up0, res_up_last = 0, dold_top = HINF, dold_bot = HINF;
+#pragma unroll 4
+    for (int i = 0; i < BR; ++i) {
+        const int y = T.y0 + i;
+        const bool rowok = y < D.rows;
+        const size_t idx = (size_t)y * pitch + T.X;
+        const bool ldc = T.inb && rowok && lane != 31;
+        const bool ldo = own && rowok;
+        const int fr = ldc ? __ldcg(FR + idx) : 0;
+        const int wh = ldc ? __ldg(WH + idx) : 0;
+        const int fd = ldo ? __ldcg(FD + idx) : 0;
+        const int wv = ldo ? __ldg(WV + idx) : 0;
+        const int rt = ldo ? __ldcg(RT + idx) : 0;
+        const int ev = ldo ? __ldcg(E + idx) : 0;
+        const int dv = (T.inb && rowok && vX) ? __ldcg(Hh + idx) : HINF;
+        const int rl = __shfl_up_sync(FULL_MASK, wh + fr, 1);
+        const unsigned bit = 1u << i;
+        bR |= (ldo && wh - fr > 0) ? bit : 0u;
+        bL |= (ldo && rl > 0) ? bit : 0u;
+        bD |= (ldo && wv - fd > 0) ? bit : 0u;
+        bU |= (ldo && prev_up > 0) ? bit : 0u;
+        bE |= (ldo && ev > 0) ? bit : 0u;
+        bQ |= (ldc && wh - fr > 0) ? bit : 0u;
+        bV |= (ldc && wh + fr > 0) ? bit : 0u;
+        prev_up = wv + fd;
+        if (i == BR - 1) res_up_last = wv + fd;     // below -> last row
+        if (i == 0) dold_top = dv;
+        if (i == BR - 1) dold_bot = dv;
+        Dl[i][lane] = (ldo && rt > 0) ? min(dv, 1) : dv;
+        if (lane == 1) S.dl0[0][i] = dv;
+        if (lane == 30) S.dl0[1][i] = dv;
+    }
 
     // d(p) <= d(q) + 1 for every residual arc p -> q, relaxed to the fixpoint
     // (ghost lanes only supply their neighbours' labels)
     bool capped = true;
-    for (int it = 0; it < 64 * TH; ++it) {
+    for (int it = 0; it < 4 * BR; ++it) {
         bool ch = false;
+        {   // vertical: a pass down and a pass up the column, 8 rows at a time
+            constexpr int CH = 8;
+            int up = hT;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BR; c0 += CH) {       // from above along arcs p -> up
+                int d[CH];
 #pragma unroll
-        for (int i = 0; i < TH; ++i) {          // from the row above (arc p -> up)
-            const int up = (i > 0) ? d[i - 1] : hT;
-            const int rU = (i > 0) ? (wv[i - 1] + fd[i - 1]) : (wvT + fdT);
-            const bool b = own && rU > 0 && up + 1 < d[i];
-            d[i] = b ? up + 1 : d[i];
-            ch |= b;
-        }
+                for (int j = 0; j < CH; ++j) d[j] = Dl[c0 + j][lane];
 #pragma unroll
-        for (int i = TH - 1; i >= 0; --i) {     // from the row below (arc p -> down)
-            const int dn = (i < TH - 1) ? d[i + 1] : hB;
-            const bool b = own && wv[i] - fd[i] > 0 && dn + 1 < d[i];
-            d[i] = b ? dn + 1 : d[i];
-            ch |= b;
-        }
-        // horizontal: if no label improves by one step from a horizontal
-        // neighbour, every row is at its horizontal fixpoint; otherwise scan
-        // all rows together (independent, so they overlap)
-        bool imp = false;
-#pragma unroll
-        for (int i = 0; i < TH; ++i) {
-            const int dr = __shfl_down_sync(FULL_MASK, d[i], 1);
-            const int dl = __shfl_up_sync(FULL_MASK, d[i], 1);
-            const int rl = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
-            imp |= own && (((wh[i] - fr[i]) > 0 && dr + 1 < d[i]) || (rl > 0 && dl + 1 < d[i]));
-        }
-        if (__any_sync(FULL_MASK, imp)) {
-#pragma unroll
-            for (int i = 0; i < TH; ++i) {
-                // from the right along runs of residual arcs p -> p+1: a
-                // segmented min-plus scan over the warp
-                int v = d[i];
-                int c = own && (wh[i] - fr[i]) > 0;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v2 = __shfl_down_sync(FULL_MASK, v, o);
-                    const int c2 = __shfl_down_sync(FULL_MASK, c, o);
-                    const bool ok = lane + o < 32;
-                    v = (ok && c && v2 + o < v) ? v2 + o : v;
-                    c = ok ? (c & c2) : 0;
+                for (int j = 0; j < CH; ++j) {
+                    const bool bb = ((bU >> (c0 + j)) & 1u) && up + 1 < d[j];
+                    d[j] = bb ? up + 1 : d[j];
+                    ch |= bb;
+                    up = d[j];
                 }
-                // from the left along runs of residual arcs p -> p-1
-                const int rl = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
-                int c3 = own && rl > 0;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v2 = __shfl_up_sync(FULL_MASK, v, o);
-                    const int c2 = __shfl_up_sync(FULL_MASK, c3, o);
-                    const bool ok = lane >= o;
-                    v = (ok && c3 && v2 + o < v) ? v2 + o : v;
-                    c3 = ok ? (c3 & c2) : 0;
-                }
-                const bool b = own && v < d[i];
-                d[i] = b ? v : d[i];
-                ch |= b;
+                for (int j = 0; j < CH; ++j) Dl[c0 + j][lane] = d[j];
             }
+            int dn = hB;
+#pragma unroll 1
+            for (int c0 = BR - CH; c0 >= 0; c0 -= CH) { // from below along arcs p -> down
+                int d[CH];
+#pragma unroll
+                for (int j = 0; j < CH; ++j) d[j] = Dl[c0 + j][lane];
+#pragma unroll
+                for (int j = CH - 1; j >= 0; --j) {
+                    const bool bb = ((bD >> (c0 + j)) & 1u) && dn + 1 < d[j];
+                    d[j] = bb ? dn + 1 : d[j];
+                    ch |= bb;
+                    dn = d[j];
+                }
+#pragma unroll
+                for (int j = 0; j < CH; ++j) Dl[c0 + j][lane] = d[j];
+            }
+        }
+        // horizontal, row by row: skip rows no label of which improves by one
+        // step from a horizontal neighbour, scan the others
+#pragma unroll 1
+        for (int i = 0; i < BR; ++i) {
+            int v = Dl[i][lane];
+            const int dr = __shfl_down_sync(FULL_MASK, v, 1);
+            const int dl = __shfl_up_sync(FULL_MASK, v, 1);
+            const bool imp = (((bR >> i) & 1u) && dr + 1 < v) || (((bL >> i) & 1u) && dl + 1 < v);
+            if (!__any_sync(FULL_MASK, imp)) continue;
+            // from the right along runs of arcs p -> p+1: segmented min-plus scan
+            int c = (bR >> i) & 1u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v2 = __shfl_down_sync(FULL_MASK, v, o);
+                const int c2 = __shfl_down_sync(FULL_MASK, c, o);
+                const bool ok = lane + o < 32;
+                v = (ok && c && v2 + o < v) ? v2 + o : v;
+                c = ok ? (c & c2) : 0;
+            }
+            // from the left along runs of arcs p -> p-1
+            int c3 = (bL >> i) & 1u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v2 = __shfl_up_sync(FULL_MASK, v, o);
+                const int c2 = __shfl_up_sync(FULL_MASK, c3, o);
+                const bool ok = lane >= o;
+                v = (ok && c3 && v2 + o < v) ? v2 + o : v;
+                c3 = ok ? (c3 & c2) : 0;
+            }
+            const bool bb = own && v < Dl[i][lane];
+            if (bb) Dl[i][lane] = v;
+            ch |= bb;
         }
         if (!__any_sync(FULL_MASK, ch)) { capped = false; break; }
     }
     self_again = capped;
 
-    // which neighbours can now improve: a border pixel p got a smaller label
-    // than the neighbour q could have read, q -> p is residual and q's label
-    // is above d(p) + 1
+    // which neighbouring strips can now improve: a border pixel p got a smaller
+    // label than the neighbour q could have read, q -> p is residual and q's
+    // label is above d(p) + 1
     bool wT = false, wB = false, wL = false, wR = false;
-    if (own && T.y0 > 0) wT = d[0] < dold[0] && (wvT - fdT) > 0 && d[0] + 1 < hT;
-    if (own && T.ty < D.tiles_y - 1) wB = d[TH - 1] < dold[TH - 1] && (wv[TH - 1] + fd[TH - 1]) > 0 && d[TH - 1] + 1 < hB;
-#pragma unroll
-    for (int i = 0; i < TH; ++i) {
-        const int qd_l = __shfl_up_sync(FULL_MASK, d[i], 1);              // lane 0's label, seen by lane 1
-        const int qr_l = __shfl_up_sync(FULL_MASK, wh[i] - fr[i], 1);     // residual lane0 -> lane1
-        const int qd_r = __shfl_down_sync(FULL_MASK, d[i], 1);            // lane 31's label, seen by lane 30
-        const bool imp_i = d[i] < dold[i];
-        wL |= own && lane == 1 && T.tx > 0 && imp_i && qr_l > 0 && d[i] + 1 < qd_l;
-        wR |= own && lane == 30 && T.tx < D.tiles_x - 1 && imp_i && (wh[i] + fr[i]) > 0 && d[i] + 1 < qd_r;
+    const int d_top = Dl[0][lane], d_bot = Dl[BR - 1][lane];
+    if (own && T.y0 > 0) wT = d_top < dold_top && res_down_above > 0 && d_top + 1 < hT;
+    if (own && below && T.ty + SPAN < D.tiles_y)
+        wB = d_bot < dold_bot && res_up_last > 0 && d_bot + 1 < hB;
+    const unsigned qbits = __shfl_up_sync(FULL_MASK, bQ, 1);     // lane 0's arcs into lane 1
+#pragma unroll 4
+    for (int i = 0; i < BR; ++i) {
+        const int di = Dl[i][lane];
+        const int qd_l = __shfl_up_sync(FULL_MASK, di, 1);
+        const int qd_r = __shfl_down_sync(FULL_MASK, di, 1);
+        if (lane == 1 && own && T.tx > 0)
+            wL |= di < S.dl0[0][i] && ((qbits >> i) & 1u) && di + 1 < qd_l;
+        if (lane == 30 && own && T.tx < D.tiles_x - 1)
+            wR |= di < S.dl0[1][i] && ((bV >> i) & 1u) && di + 1 < qd_r;
     }
     unsigned nb = 0;
     if (__any_sync(FULL_MASK, wT)) nb |= 1;
@@ -798,21 +853,24 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     if (__any_sync(FULL_MASK, wR)) nb |= 8;
     nbmask = nb;
 
-    // labels, mask of lambda_k, active count
+    // labels, mask of lambda_k, active counts of the member tiles
     uint8_t *M = P.masks + D.mask_off + (size_t)kcur * PS;
-    int cnt = 0;
+    int cnt[SPAN];
 #pragma unroll
-    for (int i = 0; i < TH; ++i) {
-        const size_t idx = (size_t)(T.y0 + i) * pitch + T.X;
-        if (own) {
-            __stcg(Hh + idx, d[i]);
-            M[idx] = d[i] >= HINF ? 1 : 0;
-        }
-        cnt += __popc(__ballot_sync(FULL_MASK, ((epos >> i) & 1u) && d[i] < HINF));
-    }
+    for (int j = 0; j < SPAN; ++j) cnt[j] = 0;
     int dm = 0;
 #pragma unroll
-    for (int i = 0; i < TH; ++i) dm = (own && d[i] < HINF) ? max(dm, d[i]) : dm;
+    for (int i = 0; i < BR; ++i) {
+        const int y = T.y0 + i;
+        const size_t idx = (size_t)y * pitch + T.X;
+        const int di = Dl[i][lane];
+        if (own && y < D.rows) {
+            __stcg(Hh + idx, di);
+            M[idx] = di >= HINF ? 1 : 0;
+            dm = di < HINF ? max(dm, di) : dm;
+        }
+        cnt[i / TH] += __popc(__ballot_sync(FULL_MASK, ((bE >> i) & 1u) && di < HINF));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dm = max(dm, __shfl_down_sync(FULL_MASK, dm, o));
     __threadfence();
@@ -820,11 +878,18 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     if (lane == 0) {
         if (dm > 0) atomicMax(&P.ist[inst].dmax, dm);
         *(volatile int *)&TS->epoch = epoch;
-        // the previous count may have been written from another SM: read it
-        // past L1 (a stale L1 line would corrupt the instance's active total)
-        const int old = ldv(&TS->active);
-        TS->active = cnt;
-        if (cnt != old) atomicAdd(&P.ist[inst].active, cnt - old);
+        int delta = 0;
+#pragma unroll
+        for (int j = 0; j < SPAN; ++j) {
+            if (T.ty + j >= D.tiles_y) break;
+            int *act = &P.tiles[g + j * D.tiles_x].active;
+            // the previous count may have been written from another SM: read
+            // it past L1 (a stale line would corrupt the instance's total)
+            const int old = ldv(act);
+            *(volatile int *)act = cnt[j];
+            delta += cnt[j] - old;
+        }
+        if (delta) atomicAdd(&P.ist[inst].active, delta);
         atomicAdd(&P.ist[inst].bfs_visits, 1ULL);
     }
 }
@@ -939,18 +1004,27 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const size_t cap = (size_t)P.ring_mask + 1;
-    for (size_t i = t0; i < cap; i += stride) P.ring[i] = (i < (size_t)P.n_tiles_total) ? (int)i : -1;
-    for (size_t i = t0; i < (size_t)P.n_tiles_total; i += stride) {
-        TileState t;
-        t.state = T_QUEUED;
-        t.epoch = 0;
-        t.lam = 0;
-        t.active = 0;
-        P.tiles[i] = t;
-    }
+    // every relabel strip of every instance is queued for the first relabel
+    for (size_t i = t0; i < cap; i += stride)
+        if (i >= (size_t)P.n_leads_total) P.ring[i] = -1;
+
+    const int span = BFS_ROWS / P.tile_h;
     for (size_t i = t0; i < (size_t)P.n_inst; i += stride) {
         const DevInst D = P.inst[i];
-        for (int j = 0; j < D.n_tiles; ++j) ((int32_t *)P.tile_inst)[D.tile_base + j] = (int)i;
+        // one thread per instance writes all of its tiles (ordered writes)
+        int l = 0;
+        for (int j = 0; j < D.n_tiles; ++j) {
+            const int g = D.tile_base + j;
+            ((int32_t *)P.tile_inst)[g] = (int)i;
+            const bool lead = ((j / D.tiles_x) % span) == 0;
+            TileState t;
+            t.state = lead ? T_QUEUED : T_IDLE;
+            t.epoch = 0;
+            t.lam = 0;
+            t.active = 0;
+            P.tiles[g] = t;
+            if (lead) P.ring[D.lead_base + l++] = g;
+        }
         InstState s;
         s.phase = PH_BFS;
         s.k = 0;
@@ -965,7 +1039,7 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
         s.lab_cap = D.hcap;
         s.step_mark = 0;
         s.epochs = 1;
-        s.outstanding = D.n_tiles;
+        s.outstanding = D.n_leads;
         s.active = 0;
         s.want_bfs = 0;
         s.flow = 0;
@@ -976,7 +1050,7 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
     if (t0 == 0) {
         Globals *G = P.g;
         G->head = 0;
-        G->tail = (unsigned long long)P.n_tiles_total;
+        G->tail = (unsigned long long)P.n_leads_total;
         G->inst_done = 0;
         G->err = 0;
         G->round_mode = 0;

@@ -111,6 +111,8 @@ extern "C" PMF_API pmf_status pmf_solve_noalloc(int32_t H, int32_t W, const int3
     d.n_tiles = n_tiles;
     d.n_lambda = n_lambda;
     d.hcap = H * W + 1;
+    d.lead_base = 0;
+    d.n_leads = tiles_x * ((tiles_y + BFS_ROWS / kTileH - 1) / (BFS_ROWS / kTileH));
 
     Params P;
     std::memset(&P, 0, sizeof(P));
@@ -131,6 +133,7 @@ extern "C" PMF_API pmf_status pmf_solve_noalloc(int32_t H, int32_t W, const int3
     P.ring_mask = (unsigned long long)(ring_cap - 1);
     P.n_inst = 1;
     P.n_tiles_total = n_tiles;
+    P.n_leads_total = d.n_leads;
     P.max_lambdas = n_lambda;
     P.sweeps = 8;
     P.relabel_pct = 200;
