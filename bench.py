@@ -33,9 +33,11 @@ from paper_1509_06004_b300 import inputs  # noqa: E402
 
 METRIC = "pixel-solves/s and solves/s, batched vs per-solve launch; serving p50/p99 latency"
 UNIT = "pixel-solves/s"
-# algorithmic bytes per tile-pixel visit of the worker kernel
+# algorithmic bytes per pixel of one worker-kernel visit: a push/relabel visit
+# covers a 30 x tile_h tile, a global-relabel visit a 30 x 32 strip
 PR_BYTES_PER_PX = 48    # reads e, h, rt, fR, fD, w_h, w_v (28 B); writes e, h, rt, fR, fD (20 B)
 BFS_BYTES_PER_PX = 33   # reads e, rt, fR, fD, h, w_h, w_v (28 B); writes h (4 B) and the mask (1 B)
+BFS_STRIP_PX = 30 * 32
 L2_FLUSH_BYTES = 512 << 20
 
 WORKLOADS = {
@@ -249,7 +251,7 @@ def run_ours(args, rank, world, dev):
     solves_s = world * wl.n_solves * args.steps / total_s
 
     # roofline of the dominant kernel (the persistent worker)
-    alg_bytes = (PR_BYTES_PER_PX * pr_v + BFS_BYTES_PER_PX * bfs_v) * tile_px / args.steps
+    alg_bytes = (PR_BYTES_PER_PX * pr_v * tile_px + BFS_BYTES_PER_PX * bfs_v * BFS_STRIP_PX) / args.steps
     wk_ms = float(np.mean(worker_ms))
     achieved = alg_bytes / (wk_ms / 1e3) / 1e9
     peaks = {}
@@ -274,7 +276,7 @@ def run_ours(args, rank, world, dev):
                      "kernel": "worker_kernel (persistent push/relabel + global relabel)",
                      "worker_ms": wk_ms, "alg_bytes_per_launch": alg_bytes,
                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                     "tile_visits_per_launch": {"push_relabel": pr_v / args.steps, "bfs": bfs_v / args.steps}},
+                     "visits_per_launch": {"push_relabel_tiles": pr_v / args.steps, "bfs_strips": bfs_v / args.steps}},
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
     }

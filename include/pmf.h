@@ -68,7 +68,9 @@ typedef enum {
     PMF_ERR_NOT_MONOTONE = 3,   /* decreasing lambda schedule or negative slope */
     PMF_ERR_OVERFLOW = 4,       /* a capacity above PMF_INF / PMF_MAX_PAIRWISE */
     PMF_ERR_CUDA = 5,           /* a CUDA runtime call failed */
-    PMF_ERR_NOT_CONVERGED = 6,  /* the device watchdog stopped this instance */
+    PMF_ERR_NOT_CONVERGED = 6,  /* the device watchdog stopped this instance; or a
+                                   scheduler self-check failed, and then every
+                                   instance of the launch reports it */
     PMF_ERR_NOT_READY = 7       /* results requested before a finished solve */
 } pmf_status;
 

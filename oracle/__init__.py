@@ -13,6 +13,10 @@ Contents
   * ``grid_solve_many``  many grid (instance, lambda) jobs on a thread pool.
   * ``brute_force_*``    enumeration of every s-t cut of a graph with at most
                          16 non-terminal nodes (numpy, exact).
+  * ``grid_flow_value``  checks that per-arc flows on a grid form a feasible
+                         s-t flow (capacity bounds and conservation) and
+                         returns its value; ``grid_arc_flows`` gives such
+                         flows from the oracle's own solver.
 
 The definitions follow Section 2 of the paper: an s-t cut splits the nodes into
 an s side and a t side, its cost is the total capacity of arcs from the s side
@@ -250,3 +254,76 @@ def brute_force_grid(H, W, w_h, w_v, src0, slope, sink, lam):
     for p in range(N):
         union[p] = 1 if np.any((arg >> p) & 1) else 0
     return best, union.reshape(H, W), len(arg)
+
+
+# ----------------------------------------------------------------------------
+# per-arc flows on a grid
+# ----------------------------------------------------------------------------
+
+class FlowError(AssertionError):
+    """Per-arc flows that are not a feasible s-t flow."""
+
+
+def grid_flow_value(H, W, w_h, w_v, src0, slope, sink, lam, f_h, f_v, f_s, f_t) -> int:
+    """Value of a grid s-t flow given per arc (Section 2's graph: arcs s->p of
+    capacity cs(p) = src0 + slope*lam, p->t of capacity sink, and each pair of
+    4-neighbours joined both ways with capacity w).  Flows are int arrays
+    [H, W]: f_s on s->p, f_t on p->t, and on each neighbour pair its net flow,
+    f_h from (y, x) to (y, x+1) and f_v from (y, x) to (y+1, x) (negative =
+    the other way; a net flow between -w and w is a flow on one of the two
+    opposite arcs within its capacity).
+
+    A flow is feasible when every arc carries between zero and its capacity
+    and, at every pixel, the flow in equals the flow out.  Its value is the
+    total flow into t.  Raises FlowError naming the first violated condition."""
+    i64 = lambda a: np.asarray(a, np.int64).reshape(H, W)
+    w_h, w_v, ct = i64(w_h), i64(w_v), i64(sink)
+    cs = i64(src0) + i64(slope) * int(lam)
+    f_h, f_v, f_s, f_t = i64(f_h), i64(f_v), i64(f_s), i64(f_t)
+    if np.any(f_s < 0) or np.any(f_s > cs):
+        raise FlowError("source arc flow outside [0, cs]")
+    if np.any(f_t < 0) or np.any(f_t > ct):
+        raise FlowError("sink arc flow outside [0, ct]")
+    if np.any(np.abs(f_h[:, :-1]) > w_h[:, :-1]) or np.any(f_h[:, -1] != 0):
+        raise FlowError("horizontal pair flow above its capacity (or past the last column)")
+    if np.any(np.abs(f_v[:-1, :]) > w_v[:-1, :]) or np.any(f_v[-1, :] != 0):
+        raise FlowError("vertical pair flow above its capacity (or past the last row)")
+    inflow = f_s.copy()
+    outflow = f_t.copy()
+    # a positive net pair flow leaves its first pixel and enters its second
+    outflow[:, :-1] += f_h[:, :-1]
+    inflow[:, 1:] += f_h[:, :-1]
+    outflow[:-1, :] += f_v[:-1, :]
+    inflow[1:, :] += f_v[:-1, :]
+    if not np.array_equal(inflow, outflow):
+        y, x = np.argwhere(inflow != outflow)[0]
+        raise FlowError(f"flow not conserved at pixel ({y}, {x})")
+    return int(f_t.sum())
+
+
+def grid_arc_flows(H, W, w_h, w_v, src0, slope, sink, lam, algo: str = "dinic"):
+    """A maximum flow of one grid instance from the oracle's digraph solver,
+    in the per-pair form of ``grid_flow_value``: (value, f_h, f_v, f_s, f_t)."""
+    tail, head, cap = grid_arcs(H, W, w_h, w_v, src0, slope, sink, lam)
+    N = H * W
+    val, fl, _ = maxflow(N + 2, tail, head, cap, N, N + 1, algo)
+    f_h = np.zeros(N, np.int64)
+    f_v = np.zeros(N, np.int64)
+    f_s = np.zeros(N, np.int64)
+    f_t = np.zeros(N, np.int64)
+    for u, v, f in zip(tail.tolist(), head.tolist(), fl.tolist()):
+        if u == N:
+            f_s[v] += f
+        elif v == N + 1:
+            f_t[u] += f
+        elif u // W == v // W:          # same row: a horizontal pair
+            if v == u + 1:
+                f_h[u] += f
+            else:
+                f_h[v] -= f
+        elif v == u + W:                # a vertical pair
+            f_v[u] += f
+        else:
+            f_v[v] -= f
+    r = lambda a: a.reshape(H, W)
+    return val, r(f_h), r(f_v), r(f_s), r(f_t)

@@ -33,8 +33,8 @@ DEFAULTS = {"tile_h": 8, "sweeps": 8, "relabel_every": 800, "label_slack": 16}
 SPACE = {
     "tile_h": [4, 8],
     "sweeps": [4, 8, 16],
-    "relabel_every": [400, 800, 1600],
-    "label_slack": [8, 16, 32],
+    "relabel_every": [200, 400, 800, 1600],
+    "label_slack": [4, 8, 16, 32],
 }
 
 

@@ -237,7 +237,7 @@ void apply_defaults(pmf_tuning *t) {
 pmf_status refresh_geometry(pmf_batch *b, cudaStream_t s) {
     const int th = b->tune.tile_h;
     const int span = BFS_ROWS / th;
-    int base = 0, lbase = 0;
+    int base = 0;
     for (int i = 0; i < b->desc.n_inst; ++i) {
         const int im = b->inst_image[i];
         DevInst &d = b->dinst[i];
@@ -251,14 +251,25 @@ pmf_status refresh_geometry(pmf_batch *b, cudaStream_t s) {
         d.n_tiles = d.tiles_x * d.tiles_y;
         d.tile_base = base;
         base += d.n_tiles;
-        d.lead_base = lbase;
         d.n_leads = d.tiles_x * ((d.tiles_y + span - 1) / span);
-        lbase += d.n_leads;
         d.hcap = d.H * d.W + 1;
         d.plane_off = b->L.plane_off[i];
         d.img_off = b->L.img_off[im];
         d.mask_off = b->L.mask_off[i];
         b->dinst_h[i] = d;
+    }
+    // the first relabel strips enter the queue largest instance first (a
+    // longest-processing-time order: the biggest grids start earliest, so the
+    // small ones fill in at the end instead of a big one running alone)
+    std::vector<int> order(b->desc.n_inst);
+    for (int i = 0; i < b->desc.n_inst; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return b->dinst_h[a].n_tiles > b->dinst_h[c].n_tiles; });
+    int lbase = 0;
+    for (int i : order) {
+        b->dinst_h[i].lead_base = lbase;
+        b->dinst[i].lead_base = lbase;
+        lbase += b->dinst_h[i].n_leads;
     }
     b->P.n_tiles_total = base;
     b->P.n_leads_total = lbase;
@@ -618,8 +629,10 @@ pmf_status pmf_sync(pmf_batch *b, pmf_status *per_instance) {
     }
     pmf_status all = PMF_OK;
     const bool gerr = b->glob_h->err != 0;
+    const bool internal = (b->glob_h->err & GE_INTERNAL_MASK) != 0;
     for (int i = 0; i < b->desc.n_inst; ++i) {
         pmf_status st = (pmf_status)b->ist_h[i].status;
+        if (internal && st == PMF_OK) st = PMF_ERR_NOT_CONVERGED;
         if (st == PMF_OK && (b->ist_h[i].phase != PH_DONE || b->ist_h[i].k < b->last_n_lambda))
             st = PMF_ERR_NOT_CONVERGED;
         if (gerr && st == PMF_OK && b->ist_h[i].phase != PH_DONE) st = PMF_ERR_NOT_CONVERGED;

@@ -23,8 +23,10 @@ enum Plane { P_E = 0, P_H = 1, P_RT = 2, P_FR = 3, P_FD = 4, P_SRC0 = 5, P_SLOPE
 enum Phase { PH_BFS = 0, PH_PR = 1, PH_DONE = 2 };
 // tile queue states
 enum TState { T_IDLE = 0, T_QUEUED = 1, T_RUNNING = 2, T_DIRTY = 3 };
-// global error flags
-enum GErr { GE_STALL = 1, GE_RING = 2, GE_SLOT = 4, GE_TIMEOUT = 8 };
+// global error flags; GE_INTERNAL_MASK marks a broken scheduler invariant, after
+// which no instance's result is trusted
+enum GErr { GE_STALL = 1, GE_RING = 2, GE_SLOT = 4, GE_TIMEOUT = 8, GE_PHASE = 16 };
+constexpr int GE_INTERNAL_MASK = GE_RING | GE_PHASE;
 // per-instance validation flags (set by the pad/init kernels)
 enum VFlag { VF_NEG = 1, VF_OVERFLOW = 2, VF_SLOPE = 4, VF_BADCAP = 8 };
 

@@ -179,43 +179,70 @@ __device__ __forceinline__ DevInst load_inst(const Params &P, int inst) {
 // CAS from IDLE: tiles released from earlier chunks start running at once and
 // may already have woken a neighbour that this loop has not reached yet; that
 // neighbour is queued (or running) and must not be queued twice.
+constexpr int SCAN_U = 8;   // tile records each lane reads per step (loads in flight)
+
 __device__ int count_active_tiles(const Params &P, const DevInst &D) {
     const int lane = threadIdx.x & 31;
     int total = 0;
-    for (int c0 = 0; c0 < D.n_tiles; c0 += 32) {
-        const bool sel = (c0 + lane) < D.n_tiles && ldv(&P.tiles[D.tile_base + c0 + lane].active) > 0;
-        total += __popc(__ballot_sync(FULL_MASK, sel));
+    for (int c0 = 0; c0 < D.n_tiles; c0 += 32 * SCAN_U) {
+        int a[SCAN_U];
+#pragma unroll
+        for (int u = 0; u < SCAN_U; ++u) {
+            const int j = c0 + u * 32 + lane;
+            a[u] = j < D.n_tiles ? ldv(&P.tiles[D.tile_base + j].active) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < SCAN_U; ++u) total += __popc(__ballot_sync(FULL_MASK, a[u] > 0));
     }
     return total;
 }
 
+// claim the selected tiles (one per lane) and append them to the ring
+__device__ __forceinline__ void enqueue_chunk(const Params &P, int inst, int t, bool sel) {
+    const int lane = threadIdx.x & 31;
+    if (sel) sel = atomicCAS(&P.tiles[t].state, T_IDLE, T_QUEUED) == T_IDLE;
+    const unsigned m = __ballot_sync(FULL_MASK, sel);
+    const int cnt = __popc(m);
+    if (cnt == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) {
+        atomicAdd(&P.ist[inst].outstanding, cnt);
+        __threadfence();
+        base = atomicAdd(&P.g->tail, (unsigned long long)cnt);
+    }
+    base = __shfl_sync(FULL_MASK, base, 0);
+    __syncwarp();
+    if (sel) {
+        __threadfence();
+        const unsigned long long tk = base + __popc(m & ((1u << lane) - 1u));
+        volatile int *slot = (volatile int *)(P.ring + (tk & P.ring_mask));
+        int dummy;
+        if (slot_wait(P, slot, true, &dummy)) *slot = t;
+    }
+}
+
 __device__ void enqueue_tiles(const Params &P, int inst, const DevInst &D, bool only_active, bool leaders_only) {
     const int lane = threadIdx.x & 31;
-    const int span = BFS_ROWS / P.tile_h;
-    for (int c0 = 0; c0 < D.n_tiles; c0 += 32) {
-        const int t = D.tile_base + c0 + lane;
-        bool sel = (c0 + lane) < D.n_tiles;
-        if (sel && leaders_only) sel = (((c0 + lane) / D.tiles_x) % span) == 0;
-        if (sel && only_active) sel = ldv(&P.tiles[t].active) > 0;
-        if (sel) sel = atomicCAS(&P.tiles[t].state, T_IDLE, T_QUEUED) == T_IDLE;
-        const unsigned m = __ballot_sync(FULL_MASK, sel);
-        const int cnt = __popc(m);
-        if (cnt == 0) continue;
-        unsigned long long base = 0;
-        if (lane == 0) {
-            atomicAdd(&P.ist[inst].outstanding, cnt);
-            __threadfence();
-            base = atomicAdd(&P.g->tail, (unsigned long long)cnt);
+    if (leaders_only) {
+        // leader j of the relabel strips: strip row j / tiles_x, tile column j % tiles_x
+        const int span = BFS_ROWS / P.tile_h;
+        for (int c0 = 0; c0 < D.n_leads; c0 += 32) {
+            const int j = c0 + lane;
+            const int r = j / D.tiles_x;
+            const int t = D.tile_base + (r * span) * D.tiles_x + (j - r * D.tiles_x);
+            enqueue_chunk(P, inst, t, j < D.n_leads);
         }
-        base = __shfl_sync(FULL_MASK, base, 0);
-        __syncwarp();
-        if (sel) {
-            __threadfence();
-            const unsigned long long tk = base + __popc(m & ((1u << lane) - 1u));
-            volatile int *slot = (volatile int *)(P.ring + (tk & P.ring_mask));
-            int dummy;
-            if (slot_wait(P, slot, true, &dummy)) *slot = t;
+        return;
+    }
+    for (int c0 = 0; c0 < D.n_tiles; c0 += 32 * SCAN_U) {
+        bool sel[SCAN_U];
+#pragma unroll
+        for (int u = 0; u < SCAN_U; ++u) {
+            const int j = c0 + u * 32 + lane;
+            sel[u] = j < D.n_tiles && (!only_active || ldv(&P.tiles[D.tile_base + j].active) > 0);
         }
+#pragma unroll 1
+        for (int u = 0; u < SCAN_U; ++u) enqueue_chunk(P, inst, D.tile_base + c0 + u * 32 + lane, sel[u]);
     }
 }
 
@@ -234,7 +261,10 @@ __device__ void trace(const Params &P, int inst, int event, volatile InstState *
     P.trace[i] = e;
 }
 
-__device__ void transition(const Params &P, int inst) {
+// One phase change.  Returns true when the items it queued had all finished
+// before it let go of its guard: the caller is then the instance's last
+// finisher again and must run the next phase change itself.
+__device__ bool transition_once(const Params &P, int inst) {
     const int lane = threadIdx.x & 31;
     volatile InstState *S = P.ist + inst;
     const DevInst D = load_inst(P, inst);
@@ -287,7 +317,7 @@ __device__ void transition(const Params &P, int inst) {
         __threadfence();
     }
     mode = __shfl_sync(FULL_MASK, mode, 0);
-    if (!mode) return;
+    if (!mode) return false;
     // the phase's parameters are published before any of its tiles can run
     const int n = (mode == 2) ? count_active_tiles(P, D) : D.n_tiles;
     if (lane == 0 && S->phase == PH_PR) {
@@ -303,10 +333,32 @@ __device__ void transition(const Params &P, int inst) {
         const long long cap = (long long)S->dmax + P.label_slack;
         S->lab_cap = (P.label_slack <= 0 || cap >= D.hcap) ? D.hcap : (int)cap;
     }
+    // a guard item keeps the phase open while its tiles are queued: tiles of
+    // the first chunks may run and retire before later chunks are counted,
+    // and without it the instance's count could reach zero in between and a
+    // second phase change would start while this one is still queueing
+    if (lane == 0) atomicAdd(&P.ist[inst].outstanding, 1);
     __threadfence();
     __syncwarp();
     // a relabel works on strips (their leader tiles are queued); push/relabel on tiles
     enqueue_tiles(P, inst, D, mode == 2, S->phase == PH_BFS);
+    int last = 0;
+    if (lane == 0) {
+        __threadfence();
+        last = atomicAdd(&P.ist[inst].outstanding, -1) == 1;
+    }
+    return __shfl_sync(FULL_MASK, last, 0) != 0;
+}
+
+// Phase changes of an instance, run by the warp that retired its last
+// outstanding item.  Repeats while a phase ends before its own queueing did
+// (a phase with no tiles to queue, or tiles that all finished meanwhile);
+// every repetition is a phase change that the visit watchdog counts, and a
+// hard cap flags the launch if it is ever reached.
+__device__ void transition(const Params &P, int inst) {
+    for (int it = 0; it < (1 << 16); ++it)
+        if (!transition_once(P, inst)) return;
+    if ((threadIdx.x & 31) == 0) atomicOr(&P.g->err, GE_RING);
 }
 
 // finish an item: wake neighbours, requeue or retire the tile, maybe change
@@ -927,8 +979,13 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32) worker_kernel(const __grid_
                      : "l"(P.ist + inst));
         bool requeue = false;
         unsigned nb = 0;
+        // a relabel item must be a strip's leader tile: anything else means a
+        // push/relabel item outlived its phase, which the phase changes rule out
+        const bool stray = phase == PH_BFS && ((g - D.tile_base) / D.tiles_x) % (BFS_ROWS / TH) != 0;
+        if (stray && lane == 0) atomicOr(&P.g->err, GE_PHASE);
         if (status == PMF_OK && phase == PH_PR) pr_visit<TH>(P, S, g, inst, D, k, requeue, nb);
-        else if (status == PMF_OK && phase == PH_BFS) bfs_visit<TH>(P, S, g, inst, D, epoch, k, requeue, nb);
+        else if (status == PMF_OK && phase == PH_BFS && !stray)
+            bfs_visit<TH>(P, S, g, inst, D, epoch, k, requeue, nb);
         __threadfence();
         __syncwarp();
         if (prof) {

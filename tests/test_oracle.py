@@ -368,3 +368,59 @@ def test_planted_mistake_is_caught(mutant):
 
 def test_unmutated_passes_compact_pins():
     assert _pins_pass(oracle.lib())
+
+
+# --------------------------------------------------------------------------
+# per-arc flows: the feasibility checker against flows from both solvers, and
+# against planted violations
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,seed", [((1, 9), 0), ((9, 1), 1), ((4, 4), 2), ((7, 11), 3), ((12, 10), 4)])
+@pytest.mark.parametrize("algo", ["dinic", "ek"])
+def test_grid_flow_value_accepts_solver_flows(shape, seed, algo):
+    H, W = shape
+    wl = inputs.random_grid(H, W, np.random.default_rng(seed), n_lambda=2)
+    im, inst = wl.images[0], wl.instances[0]
+    for lam in inst.lambdas:
+        val, f_h, f_v, f_s, f_t = oracle.grid_arc_flows(H, W, im.w_h, im.w_v, inst.src0, inst.slope,
+                                                        inst.sink, int(lam), algo)
+        got = oracle.grid_flow_value(H, W, im.w_h, im.w_v, inst.src0, inst.slope, inst.sink, int(lam),
+                                     f_h, f_v, f_s, f_t)
+        flows, _ = oracle.grid_solve(H, W, im.w_h, im.w_v, inst.src0, inst.slope, inst.sink, [int(lam)])
+        assert got == val == int(flows[0])
+
+
+def test_grid_flow_value_rejects_violations():
+    H, W = 6, 7
+    wl = inputs.random_grid(H, W, np.random.default_rng(9), p_zero=0.0)
+    im, inst = wl.images[0], wl.instances[0]
+    lam = int(inst.lambdas[0])
+    args = (H, W, im.w_h, im.w_v, inst.src0, inst.slope, inst.sink, lam)
+    val, f_h, f_v, f_s, f_t = oracle.grid_arc_flows(*args)
+    assert oracle.grid_flow_value(*args, f_h, f_v, f_s, f_t) == val
+
+    def bad(fn):
+        a = [x.copy() for x in (f_h, f_v, f_s, f_t)]
+        fn(a)
+        with pytest.raises(oracle.FlowError):
+            oracle.grid_flow_value(*args, *a)
+
+    bad(lambda a: a[0].__setitem__((2, 3), a[0][2, 3] + 1))      # unbalanced pair flow
+    bad(lambda a: a[1].__setitem__((1, 1), a[1][1, 1] - 1))
+    bad(lambda a: a[2].__setitem__((0, 0), -1))                  # negative source-arc flow
+    bad(lambda a: a[3].__setitem__((3, 3), a[3][3, 3] + 1))      # sink flow without supply
+    bad(lambda a: a[0].__setitem__((4, W - 1), 1))               # flow past the last column
+    bad(lambda a: a[1].__setitem__((H - 1, 2), 1))               # flow past the last row
+    # a circulation around one square keeps conservation but may break a bound
+    w_h = np.asarray(im.w_h).reshape(H, W)
+    a = [x.copy() for x in (f_h, f_v, f_s, f_t)]
+    a[0][1, 1] = w_h[1, 1] + 1
+    with pytest.raises(oracle.FlowError):
+        oracle.grid_flow_value(*args, *a)
+    # and an in-bounds circulation is still a flow of the same value
+    a = [x.copy() for x in (f_h, f_v, f_s, f_t)]
+    c = 1
+    a[0][2, 2] += c; a[1][2, 3] += c; a[0][3, 2] -= c; a[1][2, 2] -= c
+    ok = (np.abs(a[0][:, :-1]) <= w_h[:, :-1]).all() and \
+         (np.abs(a[1][:-1]) <= np.asarray(im.w_v).reshape(H, W)[:-1]).all()
+    if ok:
+        assert oracle.grid_flow_value(*args, *a) == val

@@ -111,3 +111,46 @@ def test_continuous_batching_equals_alone():
         assert all(s == pmf.PMF_OK for s in status)
         for (fa, ma), f, m in zip(alone, c.flows, c.masks):
             assert np.array_equal(fa, f) and np.array_equal(ma, m)
+
+
+@pytest.mark.gpu
+def test_serving_large_mix_repeated():
+    """Four concurrent large requests at a time (images up to 800 px wide),
+    served three times over: every request must finish with the same flows
+    and masks each time, equal to solving it alone, and a sample equal to the
+    oracle.  Large, sparse phases are where a phase change queues its tiles
+    for longest, so this is the mix most likely to expose a scheduling race."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1509_06004_b300 import build, pmf
+    build.build()
+    reqs = inputs.serving_stream(rate_per_s=1000.0, n_requests=10, seed=5, max_side=800)
+    for r in reqs:       # bounded test time: at most 8 seeds, 10 lambdas per request
+        r.workload.instances = r.workload.instances[:8]
+        for inst in r.workload.instances:
+            inst.lambdas = inst.lambdas[:10]
+    runs = [serving.serve(reqs, slots=4, budget_bytes=8 << 30, realtime=False, collect=True, segments=5)
+            for _ in range(3)]
+    assert runs[0].max_concurrent >= 2
+    for i, r in enumerate(reqs):
+        status, alone = pmf.solve_workload(r.workload)
+        assert all(s == pmf.PMF_OK for s in status)
+        for run in runs:
+            c = run.completed[i]
+            for (fa, ma), f, m in zip(alone, c.flows, c.masks):
+                assert np.array_equal(fa, f) and np.array_equal(ma, m)
+    rng = np.random.default_rng(0)
+    for _ in range(2):
+        i = int(rng.integers(len(reqs)))
+        wl = reqs[i].workload
+        j = int(rng.integers(len(wl.instances)))
+        inst = wl.instances[j]
+        im = wl.images[inst.image]
+        k = int(rng.integers(len(inst.lambdas)))
+        f, m = oracle.grid_solve(im.H, im.W, im.w_h, im.w_v, inst.src0, inst.slope, inst.sink,
+                                 [int(inst.lambdas[k])])
+        c = runs[-1].completed[i]
+        assert int(c.flows[j][k]) == int(f[0])
+        assert np.array_equal(c.masks[j][k].reshape(-1), np.asarray(m[0]).reshape(-1))
