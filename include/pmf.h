@@ -206,12 +206,17 @@ PMF_API pmf_status pmf_get_timing(pmf_batch *b, float *solve_ms, float *worker_m
  * (at most 65536; later events are dropped). */
 PMF_API pmf_status pmf_get_trace(pmf_batch *b, pmf_trace_event *out, int32_t cap, int32_t *n);
 
-/* Warp-time breakdown of the last solve (tuning.trace = 1), after pmf_sync:
- * out8[0..3] = ns summed over worker warps spent waiting for work, in
- * push/relabel visits, in global-relabel visits and retiring items; out8[4] =
- * push/relabel sweeps run; out8[5..7] = SM cycles (summed over visits) of the
- * push/relabel visits' load, sweep and write-back stages. */
-PMF_API pmf_status pmf_get_profile(pmf_batch *b, uint64_t *out8);
+#define PMF_PROFILE_COUNTERS 12
+
+/* Warp-time breakdown of the last solve (tuning.trace = 1), after pmf_sync,
+ * into out[PMF_PROFILE_COUNTERS] (host): out[0..3] = ns summed over worker
+ * warps spent waiting for work, in push/relabel visits, in global-relabel
+ * visits and retiring items; out[4] = push/relabel sweeps run; out[5..7] = SM
+ * cycles (summed over visits) of the push/relabel visits' load, sweep and
+ * write-back stages; out[8..10] = the same for the relabel-strip visits'
+ * load, relaxation and write-back stages; out[11] = relaxation rounds run by
+ * the relabel-strip visits.  All zero when tracing was off. */
+PMF_API pmf_status pmf_get_profile(pmf_batch *b, uint64_t *out);
 
 /* Counters of the last solve for one instance, after pmf_sync. */
 PMF_API pmf_status pmf_get_stats(pmf_batch *b, int32_t inst, pmf_stats *out);

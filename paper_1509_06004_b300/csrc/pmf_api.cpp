@@ -717,10 +717,10 @@ pmf_status pmf_get_trace(pmf_batch *b, pmf_trace_event *out, int32_t cap, int32_
     return cuda_err(cudaMemcpy(out, b->ws + b->L.trace, sizeof(TraceEvent) * m, cudaMemcpyDeviceToHost));
 }
 
-pmf_status pmf_get_profile(pmf_batch *b, uint64_t *out8) {
-    if (!b || !out8) return PMF_ERR_INVALID_ARG;
+pmf_status pmf_get_profile(pmf_batch *b, uint64_t *out) {
+    if (!b || !out) return PMF_ERR_INVALID_ARG;
     if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
-    for (int j = 0; j < 8; ++j) out8[j] = b->tune.trace ? b->glob_h->prof[j] : 0;
+    for (int j = 0; j < PMF_PROFILE_COUNTERS; ++j) out[j] = b->tune.trace ? b->glob_h->prof[j] : 0;
     return PMF_OK;
 }
 

@@ -2,10 +2,11 @@
 // (pmf_kernels.cu).  Not part of the public interface.
 #pragma once
 #include <cstddef>
-#include <cstddef>
 #include <cstdint>
 
 #include <cuda_runtime.h>
+
+#include "pmf.h"
 
 namespace pmf {
 
@@ -96,8 +97,10 @@ struct Globals {
     // warp-time breakdown (ns summed over warps), recorded with the trace:
     // [0] waiting for work, [1] push/relabel visits, [2] relabel (BFS) visits,
     // [3] retiring items (wake-ups, requeue, phase changes), [4] sweeps run,
-    // [5..7] SM cycles in the load, sweep and write-back stages of push/relabel visits
-    unsigned long long prof[8];
+    // [5..7] SM cycles in the load, sweep and write-back stages of push/relabel visits,
+    // [8..10] the same for relabel-strip visits (load, relaxation, write-back),
+    // [11] relaxation rounds of relabel-strip visits
+    unsigned long long prof[PMF_PROFILE_COUNTERS];
 };
 
 struct Params {

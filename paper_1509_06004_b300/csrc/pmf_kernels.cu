@@ -738,6 +738,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     const int *WV = WH + PS;
     TileState *TS = P.tiles + g;
     const int vstride = SPAN * D.tiles_x;
+    const long long c_start = P.trace ? clock64() : 0;
 
     // labels of a neighbouring strip count only once it has been visited in
     // this relabel epoch (otherwise they are left over from push/relabel)
@@ -768,44 +769,64 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     // neighbour into this column (used by lane 30).  Labels live in this
     // lane's own column of the warp's shared memory.
     int(*Dl)[32] = S.d;
-    unsigned bR = 0, bL = 0, bD = 0, bU = 0, bE = 0, bQ = 0, bV = 0;
+    unsigned bR = 0, bD = 0, bU = 0, bE = 0, bQ = 0, bV = 0;
     int prev_up = res_up0, res_up_last = 0, dold_top = HINF, dold_bot = HINF;
-#pragma unroll 4
-    for (int i = 0; i < BR; ++i) {
-        const int y = T.y0 + i;
-        const bool rowok = y < D.rows;
-        const size_t idx = (size_t)y * pitch + T.X;
-        const bool ldc = T.inb && rowok && lane != 31;
-        const bool ldo = own && rowok;
-        const int fr = ldc ? __ldcg(FR + idx) : 0;
-        const int wh = ldc ? __ldg(WH + idx) : 0;
-        const int fd = ldo ? __ldcg(FD + idx) : 0;
-        const int wv = ldo ? __ldg(WV + idx) : 0;
-        const int rt = ldo ? __ldcg(RT + idx) : 0;
-        const int ev = ldo ? __ldcg(E + idx) : 0;
-        const int dv = (T.inb && rowok && vX) ? __ldcg(Hh + idx) : HINF;
-        const int rl = __shfl_up_sync(FULL_MASK, wh + fr, 1);
-        const unsigned bit = 1u << i;
-        bR |= (ldo && wh - fr > 0) ? bit : 0u;
-        bL |= (ldo && rl > 0) ? bit : 0u;
-        bD |= (ldo && wv - fd > 0) ? bit : 0u;
-        bU |= (ldo && prev_up > 0) ? bit : 0u;
-        bE |= (ldo && ev > 0) ? bit : 0u;
-        bQ |= (ldc && wh - fr > 0) ? bit : 0u;
-        bV |= (ldc && wh + fr > 0) ? bit : 0u;
-        prev_up = wv + fd;
-        if (i == BR - 1) res_up_last = wv + fd;     // below -> last row
-        if (i == 0) dold_top = dv;
-        if (i == BR - 1) dold_bot = dv;
-        Dl[i][lane] = (ldo && rt > 0) ? min(dv, 1) : dv;
-        if (lane == 1) S.dl0[0][i] = dv;
-        if (lane == 30) S.dl0[1][i] = dv;
+    // 4 rows at a time: every global load of a batch is issued before any of
+    // its results is used or written to shared memory, so a batch costs one
+    // memory round trip instead of one per row
+    constexpr int LB = 4;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BR; c0 += LB) {
+        int fr[LB], wh[LB], fd[LB], wv[LB], rt[LB], ev[LB], dv[LB];
+#pragma unroll
+        for (int j = 0; j < LB; ++j) {
+            const int y = T.y0 + c0 + j;
+            const bool rowok = y < D.rows;
+            const size_t idx = (size_t)y * pitch + T.X;
+            const bool ldc = T.inb && rowok && lane != 31;
+            const bool ldo = own && rowok;
+            fr[j] = ldc ? __ldcg(FR + idx) : 0;
+            wh[j] = ldc ? __ldg(WH + idx) : 0;
+            fd[j] = ldo ? __ldcg(FD + idx) : 0;
+            wv[j] = ldo ? __ldg(WV + idx) : 0;
+            rt[j] = ldo ? __ldcg(RT + idx) : 0;
+            ev[j] = ldo ? __ldcg(E + idx) : 0;
+            dv[j] = (T.inb && rowok && vX) ? __ldcg(Hh + idx) : HINF;
+        }
+#pragma unroll
+        for (int j = 0; j < LB; ++j) {
+            const int i = c0 + j;
+            const bool rowok = T.y0 + i < D.rows;
+            const bool ldc = T.inb && rowok && lane != 31;
+            const bool ldo = own && rowok;
+            const unsigned bit = 1u << i;
+            bR |= (ldo && wh[j] - fr[j] > 0) ? bit : 0u;
+            bD |= (ldo && wv[j] - fd[j] > 0) ? bit : 0u;
+            bU |= (ldo && prev_up > 0) ? bit : 0u;
+            bE |= (ldo && ev[j] > 0) ? bit : 0u;
+            bQ |= (ldc && wh[j] - fr[j] > 0) ? bit : 0u;
+            bV |= (ldc && wh[j] + fr[j] > 0) ? bit : 0u;
+            prev_up = wv[j] + fd[j];
+            if (i == BR - 1) res_up_last = wv[j] + fd[j];     // below -> last row
+            if (i == 0) dold_top = dv[j];
+            if (i == BR - 1) dold_bot = dv[j];
+            Dl[i][lane] = (ldo && rt[j] > 0) ? min(dv[j], 1) : dv[j];
+            if (lane == 1) S.dl0[0][i] = dv[j];
+            if (lane == 30) S.dl0[1][i] = dv[j];
+        }
     }
+    // arcs from this column to the one on its left: the left column's
+    // residual w + f towards it (bV of the lane on the left)
+    unsigned bL = __shfl_up_sync(FULL_MASK, bV, 1);
+    if (!own) bL = 0;
 
     // d(p) <= d(q) + 1 for every residual arc p -> q, relaxed to the fixpoint
     // (ghost lanes only supply their neighbours' labels)
+    const long long c_loaded = P.trace ? clock64() + (Dl[0][lane] & 0) : 0;
     bool capped = true;
+    int rounds = 0;
     for (int it = 0; it < 4 * BR; ++it) {
+        ++rounds;
         bool ch = false;
         {   // vertical: a pass down and a pass up the column, 8 rows at a time
             constexpr int CH = 8;
@@ -878,6 +899,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
         if (!__any_sync(FULL_MASK, ch)) { capped = false; break; }
     }
     self_again = capped;
+    const long long c_relaxed = P.trace ? clock64() : 0;
 
     // which neighbouring strips can now improve: a border pixel p got a smaller
     // label than the neighbour q could have read, q -> p is residual and q's
@@ -927,22 +949,33 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     for (int o = 16; o > 0; o >>= 1) dm = max(dm, __shfl_down_sync(FULL_MASK, dm, o));
     __threadfence();
     __syncwarp();
+    // member tile j's active count, lane j (the counts are warp-uniform)
+    int delta = 0;
+    if (lane < SPAN && T.ty + lane < D.tiles_y) {
+        int mine = 0;
+#pragma unroll
+        for (int j = 0; j < SPAN; ++j) mine = (j == lane) ? cnt[j] : mine;
+        int *act = &P.tiles[g + lane * D.tiles_x].active;
+        // the previous count may have been written from another SM: read it
+        // past L1 (a stale line would corrupt the instance's total)
+        const int old = ldv(act);
+        *(volatile int *)act = mine;
+        delta = mine - old;
+    }
+#pragma unroll
+    for (int o = SPAN / 2; o > 0; o >>= 1) delta += __shfl_down_sync(FULL_MASK, delta, o);
     if (lane == 0) {
         if (dm > 0) atomicMax(&P.ist[inst].dmax, dm);
         *(volatile int *)&TS->epoch = epoch;
-        int delta = 0;
-#pragma unroll
-        for (int j = 0; j < SPAN; ++j) {
-            if (T.ty + j >= D.tiles_y) break;
-            int *act = &P.tiles[g + j * D.tiles_x].active;
-            // the previous count may have been written from another SM: read
-            // it past L1 (a stale line would corrupt the instance's total)
-            const int old = ldv(act);
-            *(volatile int *)act = cnt[j];
-            delta += cnt[j] - old;
-        }
         if (delta) atomicAdd(&P.ist[inst].active, delta);
         atomicAdd(&P.ist[inst].bfs_visits, 1ULL);
+        if (P.trace) {
+            const long long c_end = clock64();
+            atomicAdd(&P.g->prof[8], (unsigned long long)(c_loaded - c_start));
+            atomicAdd(&P.g->prof[9], (unsigned long long)(c_relaxed - c_loaded));
+            atomicAdd(&P.g->prof[10], (unsigned long long)(c_end - c_relaxed));
+            atomicAdd(&P.g->prof[11], (unsigned long long)rounds);
+        }
     }
 }
 
@@ -1061,27 +1094,35 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const size_t cap = (size_t)P.ring_mask + 1;
-    // every relabel strip of every instance is queued for the first relabel
     for (size_t i = t0; i < cap; i += stride)
         if (i >= (size_t)P.n_leads_total) P.ring[i] = -1;
 
     const int span = BFS_ROWS / P.tile_h;
+    // one thread per tile: its instance is the last one whose first tile is
+    // at or before it (instances own consecutive, non-empty tile ranges)
+    for (size_t g = t0; g < (size_t)P.n_tiles_total; g += stride) {
+        int lo = 0, hi = P.n_inst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((size_t)__ldg(&P.inst[mid].tile_base) <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const int tiles_x = __ldg(&P.inst[lo].tiles_x);
+        const int j = (int)(g - (size_t)__ldg(&P.inst[lo].tile_base));
+        const int ty = j / tiles_x, tx = j - ty * tiles_x;
+        const bool lead = (ty % span) == 0;
+        ((int32_t *)P.tile_inst)[g] = lo;
+        TileState t;
+        t.state = lead ? T_QUEUED : T_IDLE;
+        t.epoch = 0;
+        t.lam = 0;
+        t.active = 0;
+        P.tiles[g] = t;
+        // every relabel strip of every instance is queued for the first relabel
+        if (lead) P.ring[__ldg(&P.inst[lo].lead_base) + (ty / span) * tiles_x + tx] = (int)g;
+    }
     for (size_t i = t0; i < (size_t)P.n_inst; i += stride) {
         const DevInst D = P.inst[i];
-        // one thread per instance writes all of its tiles (ordered writes)
-        int l = 0;
-        for (int j = 0; j < D.n_tiles; ++j) {
-            const int g = D.tile_base + j;
-            ((int32_t *)P.tile_inst)[g] = (int)i;
-            const bool lead = ((j / D.tiles_x) % span) == 0;
-            TileState t;
-            t.state = lead ? T_QUEUED : T_IDLE;
-            t.epoch = 0;
-            t.lam = 0;
-            t.active = 0;
-            P.tiles[g] = t;
-            if (lead) P.ring[D.lead_base + l++] = g;
-        }
         InstState s;
         s.phase = PH_BFS;
         s.k = 0;
@@ -1114,7 +1155,7 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
         G->round_end = G->tail;
         G->t_start = gtime_ns();
         G->trace_n = 0;
-        for (int j = 0; j < 8; ++j) G->prof[j] = 0;
+        for (int j = 0; j < PMF_PROFILE_COUNTERS; ++j) G->prof[j] = 0;
     }
 }
 

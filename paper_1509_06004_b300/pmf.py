@@ -330,10 +330,10 @@ class Batch:
 
     def profile(self) -> dict:
         """Warp-time breakdown of the last solve (needs set_tuning(trace=1))."""
-        a = (ctypes.c_uint64 * 8)()
-        _check(lib().pmf_get_profile(self._h, a), "pmf_get_profile")
         keys = ["wait_ns", "pr_ns", "bfs_ns", "retire_ns", "sweeps", "pr_load_cyc", "pr_sweep_cyc",
-                "pr_store_cyc"]
+                "pr_store_cyc", "bfs_load_cyc", "bfs_relax_cyc", "bfs_store_cyc", "bfs_rounds"]
+        a = (ctypes.c_uint64 * len(keys))()
+        _check(lib().pmf_get_profile(self._h, a), "pmf_get_profile")
         return {k: int(a[i]) for i, k in enumerate(keys)}
 
     def stats(self, inst: int) -> dict:
