@@ -111,7 +111,10 @@ typedef struct {
                                 relabel; default 16 (0 = default, -1 = off) */
     int32_t grid_blocks;     /* persistent grid size in blocks (overrides blocks_per_sm;
                                 0 = auto); lets several batches share the GPU */
-    int32_t reserved;
+    int32_t push_order;      /* order of the pushes inside a sweep: 0 = every row
+                                and pixel from the sweep's starting state (default);
+                                1 = along columns and rows, so excess that arrives
+                                can move on in the same sweep */
 } pmf_tuning;
 
 /* One instance phase change recorded on the device (tuning.trace = 1). */

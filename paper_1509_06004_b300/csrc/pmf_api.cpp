@@ -231,6 +231,7 @@ void apply_defaults(pmf_tuning *t) {
     if (t->poll_ns <= 0) t->poll_ns = 256;
     if (t->label_slack == 0) t->label_slack = 16;
     if (t->label_slack < 0) t->label_slack = -1;
+    if (t->push_order != 1) t->push_order = 0;
 }
 
 // per-instance tile geometry for the current tile height; uploads the table
@@ -542,6 +543,7 @@ pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_la
     b->P.sweeps = b->tune.sweeps;
     b->P.poll_ns = b->tune.poll_ns;
     b->P.label_slack = b->tune.label_slack < 0 ? 0 : b->tune.label_slack;
+    b->P.chain_push = b->tune.push_order;
     b->P.relabel_pct = b->tune.relabel_every;
     b->P.max_visits_per_tile = b->tune.max_visits_per_tile;
     const bool geo_changed = (b->P.tile_h != b->tune.tile_h) || (b->last_n_lambda != n_lambda);

@@ -120,7 +120,7 @@ struct Params {
     int32_t *inst_flags;         // [n_inst] validation flags of set_terminals
     unsigned long long ring_mask;
     int32_t n_inst, n_tiles_total, max_lambdas, sweeps;
-    int32_t n_leads_total, pad_l_;
+    int32_t n_leads_total, chain_push;   // chain_push: push order of the sweeps (pmf_tuning.push_order)
     int32_t relabel_pct, tile_h;
     int32_t poll_ns, label_slack;
     long long max_visits_per_tile;

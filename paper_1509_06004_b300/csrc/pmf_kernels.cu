@@ -560,47 +560,132 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
         // during the push phase, so the two ends of an edge never push
         // against each other.  Push phase: an active pixel sends excess to t
         // first, then to lower neighbours along residual arcs.
-        int dDa[TH], dUa[TH];
+        if (P.chain_push) {
+            // Chain order: excess may move on in the same sweep after it
+            // arrives.  Every push is still along a residual arc to a lower
+            // neighbour from a pixel holding the excess it sends, so this is
+            // the same push operation in a different order.
 #pragma unroll
-        for (int i = 0; i < TH; ++i) {
-            const int hp = h[i];
-            const int hL = __shfl_up_sync(FULL_MASK, hp, 1);
-            const int hR = __shfl_down_sync(FULL_MASK, hp, 1);
-            const int rL = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
-            const int hU = (i > 0) ? h[i - 1] : hT;
-            const int hD = (i < TH - 1) ? h[i + 1] : hB;
-            const int rR = wh[i] - fr[i];
-            const int rD = wv[i] - fd[i];
-            const int rU = (i > 0) ? (wv[i - 1] + fd[i - 1]) : (wvT + fdT);
-            const bool a = own && e[i] > 0 && hp < HINF;
-            int ex = a ? e[i] : 0;
-            const int dT = min(ex, rt[i]);
-            ex -= dT;
-            const int dD = (rD > 0 && hD < hp) ? min(ex, rD) : 0;
-            ex -= dD;
-            const int dR = (rR > 0 && hR < hp) ? min(ex, rR) : 0;
-            ex -= dR;
-            const int dU = (rU > 0 && hU < hp) ? min(ex, rU) : 0;
-            ex -= dU;
-            const int dL = (rL > 0 && hL < hp) ? min(ex, rL) : 0;
-            e[i] -= dT + dD + dR + dU + dL;
-            rt[i] -= dT;
-            dDa[i] = dD;
-            dUa[i] = dU;
-            // horizontal transfers stay inside the row (ghost lanes collect
-            // what crosses the tile's left and right borders)
-            fr[i] += dR;
-            const int inR = __shfl_up_sync(FULL_MASK, dR, 1);
-            const int inL = __shfl_down_sync(FULL_MASK, dL, 1);
-            e[i] += (lane > 0 ? inR : 0) + (lane < 31 ? inL : 0);
-            fr[i] -= (lane < 31 ? inL : 0);
-        }
-        // vertical transfers, after every row has decided
+            for (int i = 0; i < TH; ++i) {             // to t
+                const bool a = own && e[i] > 0 && h[i] < HINF;
+                const int dT = a ? min(e[i], rt[i]) : 0;
+                e[i] -= dT;
+                rt[i] -= dT;
+            }
 #pragma unroll
-        for (int i = 0; i < TH; ++i) {
-            fd[i] += dDa[i];
-            if (i < TH - 1) e[i + 1] += dDa[i]; else outD += dDa[i];
-            if (i > 0) { e[i - 1] += dUa[i]; fd[i - 1] -= dUa[i]; } else { outU += dUa[i]; fdT -= dUa[i]; }
+            for (int i = 0; i < TH; ++i) {             // down the column, top to bottom
+                const int hD = (i < TH - 1) ? h[i + 1] : hB;
+                const int rD = wv[i] - fd[i];
+                const bool a = own && e[i] > 0 && h[i] < HINF;
+                const int d = (a && rD > 0 && hD < h[i]) ? min(e[i], rD) : 0;
+                e[i] -= d;
+                fd[i] += d;
+                if (i < TH - 1) e[i + 1] += d; else outD += d;
+            }
+#pragma unroll
+            for (int i = TH - 1; i >= 0; --i) {        // up the column, bottom to top
+                const int hU = (i > 0) ? h[i - 1] : hT;
+                const int rU = (i > 0) ? (wv[i - 1] + fd[i - 1]) : (wvT + fdT);
+                const bool a = own && e[i] > 0 && h[i] < HINF;
+                const int d = (a && rU > 0 && hU < h[i]) ? min(e[i], rU) : 0;
+                e[i] -= d;
+                if (i > 0) { e[i - 1] += d; fd[i - 1] -= d; } else { outU += d; fdT -= d; }
+            }
+            // along the row: a pixel forwards min(its excess + what arrives
+            // from the previous pixel of the run, residual of its arc) when
+            // the arc leads to a lower neighbour.  Such maps x -> min(a + x, b)
+            // compose into the same form, (a1, b1) then (a2, b2) giving
+            // (a1 + a2, min(a2 + b1, b2)), so one warp scan yields every
+            // pixel's outflow.  a is clamped at 2^29: residuals are below
+            // 2^29, so a larger a never changes the result.
+            constexpr int ACL = 1 << 29;
+#pragma unroll
+            for (int i = 0; i < TH; ++i) {             // rightwards
+                const int hR = __shfl_down_sync(FULL_MASK, h[i], 1);
+                const int rR = wh[i] - fr[i];
+                const bool live = own && h[i] < HINF;
+                int A = live ? min(e[i], ACL) : 0;
+                int B = (live && rR > 0 && hR < h[i]) ? rR : 0;
+                if (!__any_sync(FULL_MASK, A > 0 && B > 0)) continue;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int A2 = __shfl_up_sync(FULL_MASK, A, o);
+                    const int B2 = __shfl_up_sync(FULL_MASK, B, o);
+                    if (lane >= o) {
+                        B = min(A + B2, B);
+                        A = min(A2 + A, ACL);
+                    }
+                }
+                const int out = min(A, B);
+                const int in = __shfl_up_sync(FULL_MASK, out, 1);
+                e[i] += (lane > 0 ? in : 0) - out;
+                fr[i] += out;
+            }
+#pragma unroll
+            for (int i = 0; i < TH; ++i) {             // leftwards
+                const int hL = __shfl_up_sync(FULL_MASK, h[i], 1);
+                const int rL = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
+                const bool live = own && h[i] < HINF;
+                int A = live ? min(e[i], ACL) : 0;
+                int B = (live && rL > 0 && hL < h[i]) ? rL : 0;
+                if (!__any_sync(FULL_MASK, A > 0 && B > 0)) continue;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int A2 = __shfl_down_sync(FULL_MASK, A, o);
+                    const int B2 = __shfl_down_sync(FULL_MASK, B, o);
+                    if (lane + o < 32) {
+                        B = min(A + B2, B);
+                        A = min(A2 + A, ACL);
+                    }
+                }
+                const int out = min(A, B);
+                const int in = __shfl_down_sync(FULL_MASK, out, 1);
+                e[i] += (lane < 31 ? in : 0) - out;
+                fr[i] -= (lane < 31 ? in : 0);
+            }
+        } else {
+            int dDa[TH], dUa[TH];
+    #pragma unroll
+            for (int i = 0; i < TH; ++i) {
+                const int hp = h[i];
+                const int hL = __shfl_up_sync(FULL_MASK, hp, 1);
+                const int hR = __shfl_down_sync(FULL_MASK, hp, 1);
+                const int rL = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
+                const int hU = (i > 0) ? h[i - 1] : hT;
+                const int hD = (i < TH - 1) ? h[i + 1] : hB;
+                const int rR = wh[i] - fr[i];
+                const int rD = wv[i] - fd[i];
+                const int rU = (i > 0) ? (wv[i - 1] + fd[i - 1]) : (wvT + fdT);
+                const bool a = own && e[i] > 0 && hp < HINF;
+                int ex = a ? e[i] : 0;
+                const int dT = min(ex, rt[i]);
+                ex -= dT;
+                const int dD = (rD > 0 && hD < hp) ? min(ex, rD) : 0;
+                ex -= dD;
+                const int dR = (rR > 0 && hR < hp) ? min(ex, rR) : 0;
+                ex -= dR;
+                const int dU = (rU > 0 && hU < hp) ? min(ex, rU) : 0;
+                ex -= dU;
+                const int dL = (rL > 0 && hL < hp) ? min(ex, rL) : 0;
+                e[i] -= dT + dD + dR + dU + dL;
+                rt[i] -= dT;
+                dDa[i] = dD;
+                dUa[i] = dU;
+                // horizontal transfers stay inside the row (ghost lanes collect
+                // what crosses the tile's left and right borders)
+                fr[i] += dR;
+                const int inR = __shfl_up_sync(FULL_MASK, dR, 1);
+                const int inL = __shfl_down_sync(FULL_MASK, dL, 1);
+                e[i] += (lane > 0 ? inR : 0) + (lane < 31 ? inL : 0);
+                fr[i] -= (lane < 31 ? inL : 0);
+            }
+            // vertical transfers, after every row has decided
+    #pragma unroll
+            for (int i = 0; i < TH; ++i) {
+                fd[i] += dDa[i];
+                if (i < TH - 1) e[i + 1] += dDa[i]; else outD += dDa[i];
+                if (i > 0) { e[i - 1] += dUa[i]; fd[i - 1] -= dUa[i]; } else { outU += dUa[i]; fdT -= dUa[i]; }
+            }
         }
         // relabel phase: an active pixel without an admissible arc moves to
         // one above its lowest residual neighbour (t has label 0); all rows

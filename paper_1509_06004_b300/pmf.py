@@ -67,7 +67,7 @@ class Tuning(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("trace", ctypes.c_int32),
                 ("poll_ns", ctypes.c_int32), ("label_slack", ctypes.c_int32),
-                ("grid_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32), ("push_order", ctypes.c_int32)]
 
 
 class TraceEvent(ctypes.Structure):
@@ -245,7 +245,7 @@ class Batch:
     def tuning(self) -> dict:
         t = Tuning()
         _check(lib().pmf_get_tuning(self._h, ctypes.byref(t)), "pmf_get_tuning")
-        return {f: getattr(t, f) for f, _ in Tuning._fields_ if f != "reserved"}
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
     # -- solve -------------------------------------------------------------------
     def solve(self, lambdas, stream=None):

@@ -72,7 +72,8 @@ def test_alone_equals_in_mixed_batch(P):
 @pytest.mark.parametrize("knobs", [dict(tile_h=4), dict(sweeps=1), dict(sweeps=32), dict(relabel_every=50),
                                    dict(relabel_every=5000), dict(label_slack=-1), dict(label_slack=1),
                                    dict(blocks_per_sm=1), dict(poll_ns=8192), dict(grid_blocks=1),
-                                   dict(grid_blocks=3), dict(grid_blocks=37), dict(grid_blocks=197, tile_h=4)])
+                                   dict(grid_blocks=3), dict(grid_blocks=37), dict(grid_blocks=197, tile_h=4),
+                                   dict(push_order=1), dict(push_order=1, tile_h=4, sweeps=2)])
 def test_launch_configuration_does_not_change_results(P, knobs):
     wl = _synthetic(3, 70, 96, 3, 8)
     _same(_solve(P, wl), _solve(P, wl, **knobs))

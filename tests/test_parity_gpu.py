@@ -40,11 +40,12 @@ SHAPES = [(1, 1), (1, 7), (7, 1), (3, 5), (8, 32), (9, 33), (16, 31), (17, 65), 
 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("tile_h", [4, 8])
-def test_random_small_grids(pmf, shape, tile_h):
+@pytest.mark.parametrize("push_order", [0, 1])
+def test_random_small_grids(pmf, shape, tile_h, push_order):
     H, W = shape
     rng = np.random.default_rng(H * 1000 + W)
     wl = inputs.random_grid(H, W, rng, wmax=20, tmax=40, p_zero=0.2, n_lambda=4, lam_max=30)
-    check_workload(pmf, wl, tile_h=tile_h)
+    check_workload(pmf, wl, tile_h=tile_h, push_order=push_order)
 
 
 @pytest.mark.parametrize("mode", ["persistent", "persistent-nograph", "rounds"])
