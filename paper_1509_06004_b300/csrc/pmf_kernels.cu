@@ -63,7 +63,8 @@ struct WarpSmem {
     int e0[2][TH];          // excess of lanes 1 and 30 at load
     int f0[2][TH];          // fR of lane 0 (left border edge) and lane 30 (right border edge)
     int dl0[2][BFS_ROWS];   // relabel: labels of lanes 1 and 30 at load (a strip's side columns)
-    int d[BFS_ROWS][32];    // relabel: the strip's labels, row i / lane l (each lane its own column)
+    int d[BFS_ROWS][33];    // relabel: the strip's labels, row i / column l (one pad column, so
+                            // a lane walking a row and a lane walking a column both hit 32 banks)
 };
 
 // --------------------------------------------------------------------------
@@ -853,7 +854,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     // on its right (read by lane 1 from ghost lane 0); V = arc from the right
     // neighbour into this column (used by lane 30).  Labels live in this
     // lane's own column of the warp's shared memory.
-    int(*Dl)[32] = S.d;
+    int(*Dl)[33] = S.d;
     unsigned bR = 0, bD = 0, bU = 0, bE = 0, bQ = 0, bV = 0;
     int prev_up = res_up0, res_up_last = 0, dold_top = HINF, dold_bot = HINF;
     // 4 rows at a time: every global load of a batch is issued before any of
@@ -907,6 +908,15 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
 
     // d(p) <= d(q) + 1 for every residual arc p -> q, relaxed to the fixpoint
     // (ghost lanes only supply their neighbours' labels)
+    // the same arcs by row for the transposed horizontal passes: lane i gets
+    // row i's right and left arcs as bit masks over the columns
+    unsigned rowR = 0, rowL = 0;
+#pragma unroll 4
+    for (int i = 0; i < BR; ++i) {
+        const unsigned r = __ballot_sync(FULL_MASK, (bR >> i) & 1u);
+        const unsigned l = __ballot_sync(FULL_MASK, (bL >> i) & 1u);
+        if (lane == i) { rowR = r; rowL = l; }
+    }
     const long long c_loaded = P.trace ? clock64() + (Dl[0][lane] & 0) : 0;
     bool capped = true;
     int rounds = 0;
@@ -948,39 +958,27 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
                 for (int j = 0; j < CH; ++j) Dl[c0 + j][lane] = d[j];
             }
         }
-        // horizontal, row by row: skip rows no label of which improves by one
-        // step from a horizontal neighbour, scan the others
-#pragma unroll 1
-        for (int i = 0; i < BR; ++i) {
-            int v = Dl[i][lane];
-            const int dr = __shfl_down_sync(FULL_MASK, v, 1);
-            const int dl = __shfl_up_sync(FULL_MASK, v, 1);
-            const bool imp = (((bR >> i) & 1u) && dr + 1 < v) || (((bL >> i) & 1u) && dl + 1 < v);
-            if (!__any_sync(FULL_MASK, imp)) continue;
-            // from the right along runs of arcs p -> p+1: segmented min-plus scan
-            int c = (bR >> i) & 1u;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v2 = __shfl_down_sync(FULL_MASK, v, o);
-                const int c2 = __shfl_down_sync(FULL_MASK, c, o);
-                const bool ok = lane + o < 32;
-                v = (ok && c && v2 + o < v) ? v2 + o : v;
-                c = ok ? (c & c2) : 0;
+        // horizontal, transposed: lane i walks row i left to right along arcs
+        // p -> p-1 and back along arcs p -> p+1 (ghost columns 0 and 31 have
+        // no arcs of their own, so they only pass their labels in)
+        __syncwarp();
+        if (lane < BR) {
+            int prev = Dl[lane][0];
+#pragma unroll 8
+            for (int c = 1; c < 32; ++c) {
+                int v = Dl[lane][c];
+                if (((rowL >> c) & 1u) && prev + 1 < v) { v = prev + 1; Dl[lane][c] = v; ch = true; }
+                prev = v;
             }
-            // from the left along runs of arcs p -> p-1
-            int c3 = (bL >> i) & 1u;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v2 = __shfl_up_sync(FULL_MASK, v, o);
-                const int c2 = __shfl_up_sync(FULL_MASK, c3, o);
-                const bool ok = lane >= o;
-                v = (ok && c3 && v2 + o < v) ? v2 + o : v;
-                c3 = ok ? (c3 & c2) : 0;
+            prev = Dl[lane][31];
+#pragma unroll 8
+            for (int c = 30; c >= 0; --c) {
+                int v = Dl[lane][c];
+                if (((rowR >> c) & 1u) && prev + 1 < v) { v = prev + 1; Dl[lane][c] = v; ch = true; }
+                prev = v;
             }
-            const bool bb = own && v < Dl[i][lane];
-            if (bb) Dl[i][lane] = v;
-            ch |= bb;
         }
+        __syncwarp();
         if (!__any_sync(FULL_MASK, ch)) { capped = false; break; }
     }
     self_again = capped;
@@ -995,15 +993,17 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     if (own && below && T.ty + SPAN < D.tiles_y)
         wB = d_bot < dold_bot && res_up_last > 0 && d_bot + 1 < hB;
     const unsigned qbits = __shfl_up_sync(FULL_MASK, bQ, 1);     // lane 0's arcs into lane 1
-#pragma unroll 4
-    for (int i = 0; i < BR; ++i) {
-        const int di = Dl[i][lane];
-        const int qd_l = __shfl_up_sync(FULL_MASK, di, 1);
-        const int qd_r = __shfl_down_sync(FULL_MASK, di, 1);
-        if (lane == 1 && own && T.tx > 0)
-            wL |= di < S.dl0[0][i] && ((qbits >> i) & 1u) && di + 1 < qd_l;
-        if (lane == 30 && own && T.tx < D.tiles_x - 1)
-            wR |= di < S.dl0[1][i] && ((bV >> i) & 1u) && di + 1 < qd_r;
+    // lanes 1 and 30 compare their column with the ghost column beside it
+    if ((lane == 1 && own && T.tx > 0) || (lane == 30 && own && T.tx < D.tiles_x - 1)) {
+        const int side = lane == 1 ? 0 : 1, q = lane == 1 ? 0 : 31;
+        const unsigned arcs = lane == 1 ? qbits : bV;
+        bool w = false;
+#pragma unroll 8
+        for (int i = 0; i < BR; ++i) {
+            const int di = Dl[i][lane];
+            w |= di < S.dl0[side][i] && ((arcs >> i) & 1u) && di + 1 < Dl[i][q];
+        }
+        if (lane == 1) wL = w; else wR = w;
     }
     unsigned nb = 0;
     if (__any_sync(FULL_MASK, wT)) nb |= 1;
@@ -1014,11 +1014,9 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
 
     // labels, mask of lambda_k, active counts of the member tiles
     uint8_t *M = P.masks + D.mask_off + (size_t)kcur * PS;
-    int cnt[SPAN];
-#pragma unroll
-    for (int j = 0; j < SPAN; ++j) cnt[j] = 0;
+    unsigned live = 0;      // bit i: row i's label is finite
     int dm = 0;
-#pragma unroll
+#pragma unroll 8
     for (int i = 0; i < BR; ++i) {
         const int y = T.y0 + i;
         const size_t idx = (size_t)y * pitch + T.X;
@@ -1028,10 +1026,15 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
             M[idx] = di >= HINF ? 1 : 0;
             dm = di < HINF ? max(dm, di) : dm;
         }
-        cnt[i / TH] += __popc(__ballot_sync(FULL_MASK, ((bE >> i) & 1u) && di < HINF));
+        live |= di < HINF ? (1u << i) : 0u;
     }
+    // active pixels (positive excess, finite label) of each member tile
+    int cnt[SPAN];
+    constexpr unsigned TMASK = (TH == 32) ? 0xffffffffu : ((1u << TH) - 1u);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dm = max(dm, __shfl_down_sync(FULL_MASK, dm, o));
+    for (int j = 0; j < SPAN; ++j)
+        cnt[j] = (int)__reduce_add_sync(FULL_MASK, (unsigned)__popc(bE & live & (TMASK << (j * TH))));
+    dm = (int)__reduce_max_sync(FULL_MASK, (unsigned)dm);
     __threadfence();
     __syncwarp();
     // member tile j's active count, lane j (the counts are warp-uniform)
@@ -1070,7 +1073,9 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
 constexpr int WORKER_WARPS = 4;
 
 template <int TH>
-__global__ void __launch_bounds__(WORKER_WARPS * 32) worker_kernel(const __grid_constant__ Params P) {
+// at least 4 resident blocks per SM at tile height 4 (128 registers) and 2 at
+// height 8: with fewer, throughput-bound batches lose more than the spills cost
+__global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_kernel(const __grid_constant__ Params P) {
     __shared__ WarpSmem<TH> smem[WORKER_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<TH> &S = smem[w];
