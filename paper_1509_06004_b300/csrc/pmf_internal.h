@@ -93,6 +93,7 @@ struct Globals {
     alignas(128) int32_t err, round_mode;
     unsigned long long round_end;
     unsigned long long t_start;      // %globaltimer at the start of the launch
+    unsigned long long progress;     // bumped by warps running kept items (no queue traffic)
     alignas(128) unsigned long long trace_n;
     // warp-time breakdown (ns summed over warps), recorded with the trace:
     // [0] waiting for work, [1] push/relabel visits, [2] relabel (BFS) visits,

@@ -106,7 +106,7 @@ __device__ int ring_pop_ticket(const Params &P) {   // one lane; -1 = stop
     const unsigned long long h = atomicAdd(&G->head, 1ULL);
     volatile int *slot = (volatile int *)(P.ring + (h & P.ring_mask));
     unsigned ns = 32;
-    unsigned long long last_tail = ~0ULL, t_since = 0;
+    unsigned long long last_tail = ~0ULL, last_prog = ~0ULL, t_since = 0;
     int last_pend = -1;
     for (unsigned polls = 1;; ++polls) {
         const int v = *slot;
@@ -124,10 +124,11 @@ __device__ int ring_pop_ticket(const Params &P) {   // one lane; -1 = stop
                 atomicOr(&G->err, GE_TIMEOUT);
                 return -1;
             }
-            const unsigned long long tl = ldv64(&G->tail);
-            if (tl != last_tail || ndone != last_pend) {
+            const unsigned long long tl = ldv64(&G->tail), pg = ldv64(&G->progress);
+            if (tl != last_tail || ndone != last_pend || pg != last_prog) {
                 last_tail = tl;
                 last_pend = ndone;
+                last_prog = pg;
                 t_since = now;
             } else if (now - t_since > (unsigned long long)P.stall_ns) {
                 atomicOr(&G->err, GE_STALL);
@@ -366,8 +367,13 @@ __device__ void transition(const Params &P, int inst) {
 // the instance's phase.  Lanes 0-3 wake the four neighbours in parallel, lane 4
 // settles this tile; the instance's outstanding count changes once by the net
 // number of items (pushed - 1), BEFORE the new items become visible.
-__device__ void finish(const Params &P, int g, int inst, int phase, bool requeue, unsigned nb,
-                       const DevInst &D) {
+// With keep set, one new item (this tile if it runs again, else the first
+// woken neighbour) is returned to the caller, which runs it next on the same
+// warp instead of queueing it: chains of dependent visits then stay on an SM
+// whose caches hold the code and the neighbourhood (the queue otherwise hands
+// an item to the warp that has been idle longest).  Returns -1 otherwise.
+__device__ int finish(const Params &P, int g, int inst, int phase, bool requeue, unsigned nb,
+                      const DevInst &D, bool keep) {
     const int lane = threadIdx.x & 31;
     volatile InstState *IS = P.ist + inst;
     bool allow = false;
@@ -410,8 +416,13 @@ __device__ void finish(const Params &P, int g, int inst, int phase, bool requeue
             }
         }
     }
-    const unsigned pm = __ballot_sync(FULL_MASK, item >= 0);
-    const int k = __popc(pm);
+    const unsigned pm_all = __ballot_sync(FULL_MASK, item >= 0);
+    const int k = __popc(pm_all);
+    // the kept item: lane 4 (this tile) if set, else the lowest lane's
+    const int kl = !keep || pm_all == 0 ? -1 : ((pm_all >> 4) & 1u) ? 4 : __ffs(pm_all) - 1;
+    const int kept = kl >= 0 ? __shfl_sync(FULL_MASK, item, kl) : -1;
+    const unsigned pm = kl >= 0 ? pm_all & ~(1u << kl) : pm_all;
+    const int kq = __popc(pm);           // items for the ring
     int trans = 0;
     unsigned long long base = 0;
     if (lane == 0) {
@@ -420,21 +431,22 @@ __device__ void finish(const Params &P, int g, int inst, int phase, bool requeue
             const int old = atomicAdd(&P.ist[inst].outstanding, delta);
             trans = (old + delta == 0);
         }
-        if (k) {
+        if (kq) {
             __threadfence();
-            base = atomicAdd(&P.g->tail, (unsigned long long)k);
+            base = atomicAdd(&P.g->tail, (unsigned long long)kq);
         }
     }
     base = __shfl_sync(FULL_MASK, base, 0);
     trans = __shfl_sync(FULL_MASK, trans, 0);
     __syncwarp();
-    if (item >= 0) {
+    if ((pm >> lane) & 1u) {
         const unsigned long long tk = base + __popc(pm & ((1u << lane) - 1u));
         volatile int *slot = (volatile int *)(P.ring + (tk & P.ring_mask));
         int dummy;
         if (slot_wait(P, slot, true, &dummy)) *slot = item;
     }
-    if (trans) transition(P, inst);
+    if (trans) transition(P, inst);      // only when k == 0, so nothing is kept
+    return kept;
 }
 
 // --------------------------------------------------------------------------
@@ -1082,10 +1094,28 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_ker
     const int round_mode = ldv(&P.g->round_mode);
     const bool prof = P.trace != nullptr;
     unsigned long long tw = 0, tpr = 0, tbfs = 0, tfin = 0, t0 = prof ? gtime_ns() : 0;
+    int next = -1;           // an item kept by the last finish, run without queueing
+    unsigned chain = 0;
     for (;;) {
         int g = 0;
-        if (lane == 0) g = round_mode ? ring_pop_round(P) : ring_pop_ticket(P);
-        g = __shfl_sync(FULL_MASK, g, 0);
+        if (next >= 0) {
+            g = next;
+            next = -1;
+            // a long chain of kept items still notices a launch-wide stop,
+            // and shows the stall watchdog that work is being done
+            if ((++chain & 15) == 0) {
+                int stop = 0;
+                if (lane == 0) {
+                    atomicAdd(&P.g->progress, 1ULL);
+                    stop = ldv(&P.g->err);
+                }
+                if (__shfl_sync(FULL_MASK, stop, 0)) break;
+            }
+        } else {
+            chain = 0;
+            if (lane == 0) g = round_mode ? ring_pop_round(P) : ring_pop_ticket(P);
+            g = __shfl_sync(FULL_MASK, g, 0);
+        }
         if (prof) { const unsigned long long t1 = gtime_ns(); tw += t1 - t0; t0 = t1; }
         if (g < 0) break;
         const int inst = __ldg(P.tile_inst + g);
@@ -1116,7 +1146,8 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_ker
             if (phase == PH_PR) tpr += t1 - t0; else tbfs += t1 - t0;
             t0 = t1;
         }
-        finish(P, g, inst, phase, requeue, nb, D);
+        // in host-polled rounds every new item waits for the next round
+        next = finish(P, g, inst, phase, requeue, nb, D, round_mode == 0);
         if (prof) { const unsigned long long t1 = gtime_ns(); tfin += t1 - t0; t0 = t1; }
     }
     if (prof && lane == 0) {
@@ -1244,6 +1275,7 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
         G->round_mode = 0;
         G->round_end = G->tail;
         G->t_start = gtime_ns();
+        G->progress = 0;
         G->trace_n = 0;
         for (int j = 0; j < PMF_PROFILE_COUNTERS; ++j) G->prof[j] = 0;
     }
