@@ -179,7 +179,7 @@ def resolve_mode(args, wl, dev, tuning0):
         return int(args.mode[3:]), tuning0, None
     c = autotune.cached(wl, dev.index)
     if c is not None and not tuning0:
-        knobs = {k: c[k] for k in autotune.DEFAULTS}
+        knobs = {k: c.get(k, v) for k, v in autotune.DEFAULTS.items()}
         return int(c["segments"]), knobs, {"source": "autotune cache", "class": autotune.workload_class(wl),
                                            "tuned_ms": c.get("ms")}
     divs = autotune.divisors(m)
@@ -195,7 +195,8 @@ def run_ours(args, rank, world, dev):
 
     wl = WORKLOADS[args.workload](rank_seed(args.seed, rank))
     tuning0 = {k: v for k, v in (("tile_h", args.tile_h), ("sweeps", args.sweeps),
-                                 ("relabel_every", args.relabel_every)) if v}
+                                 ("relabel_every", args.relabel_every), ("label_slack", args.label_slack),
+                                 ("push_order", args.push_order)) if v}
     m = min(len(i.lambdas) for i in wl.instances)
     segments, tuning, mode_probe = resolve_mode(args, wl, dev, tuning0)
     args.mode = mode_name(segments, m)
@@ -471,6 +472,8 @@ def main(argv=None):
     ap.add_argument("--tile-h", type=int, default=0)
     ap.add_argument("--sweeps", type=int, default=0)
     ap.add_argument("--relabel-every", type=int, default=0)
+    ap.add_argument("--label-slack", type=int, default=0)
+    ap.add_argument("--push-order", type=int, default=0)
     ap.add_argument("--per-solve-sample", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")

@@ -9,7 +9,8 @@ instance count and schedule length:
   per seed; schedule length = every (seed, lambda) cold, the paper's
   lambda-supergraph); more pieces give the GPU more independent work, fewer
   keep more warm-start reuse;
-* ``tile_h`` (rows per tile), ``sweeps`` (push/relabel sweeps per tile visit),
+* ``tile_h`` (rows per tile), ``push_order`` (pushes from the sweep's starting
+  state, or along columns and rows), ``sweeps`` (push/relabel sweeps per tile visit),
   ``relabel_every`` (visit budget of a push/relabel phase, percent of its
   tiles) and ``label_slack`` (parking threshold above the last exact distance).
 
@@ -29,10 +30,11 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_PATH = os.path.join(HERE, "tuned.json")
 
-DEFAULTS = {"tile_h": 8, "sweeps": 8, "relabel_every": 800, "label_slack": 16}
+DEFAULTS = {"tile_h": 4, "sweeps": 8, "relabel_every": 800, "label_slack": 16, "push_order": 0}
 SPACE = {
     "tile_h": [4, 8],
-    "sweeps": [4, 8, 16],
+    "push_order": [0, 1],
+    "sweeps": [2, 4, 8, 16],
     "relabel_every": [200, 400, 800, 1600],
     "label_slack": [4, 8, 16, 32],
 }
