@@ -221,6 +221,25 @@ PMF_API pmf_status pmf_get_trace(pmf_batch *b, pmf_trace_event *out, int32_t cap
  * the relabel-strip visits.  All zero when tracing was off. */
 PMF_API pmf_status pmf_get_profile(pmf_batch *b, uint64_t *out);
 
+/* A feasible maximum flow of instance inst, arc by arc, at the last lambda of
+ * the most recent solve (Section 2's graph; the max-flow/min-cut theorem the
+ * paper cites there makes its value the minimum cut cost).  The solve itself
+ * ends with a maximum preflow; this call returns the excess left on pixels
+ * that cannot reach t back towards s (the second phase of push-relabel), on
+ * the GPU, without changing the instance's state, masks or flow values.
+ * Outputs are caller-owned DEVICE arrays of H*W int32, row-major (y*W + x):
+ *   f_h  net flow from (y,x) to (y,x+1), negative = leftwards; 0 in the last column
+ *   f_v  net flow from (y,x) to (y+1,x), negative = upwards; 0 in the last row
+ *   f_s  flow on the arc s -> (y,x), 0 <= f_s <= cs(y,x,lambda)
+ *   f_t  flow on the arc (y,x) -> t, 0 <= f_t <= ct(y,x)
+ * with |f_h| <= w_h, |f_v| <= w_v, flow in = flow out at every pixel and
+ * sum(f_t) = pmf_get_flow of the last lambda.  Several maximum flows exist;
+ * any one is returned.  Synchronous.  PMF_ERR_NOT_READY before a finished
+ * solve or for a failed instance, PMF_ERR_NOT_CONVERGED if the return did not
+ * finish within its sweep limit (2^17 sweeps). */
+PMF_API pmf_status pmf_get_flow_arcs(pmf_batch *b, int32_t inst, int32_t *f_h, int32_t *f_v, int32_t *f_s,
+                                     int32_t *f_t);
+
 /* Counters of the last solve for one instance, after pmf_sync. */
 PMF_API pmf_status pmf_get_stats(pmf_batch *b, int32_t inst, pmf_stats *out);
 

@@ -28,7 +28,7 @@ int round_up_i(int v, int a) { return (v + a - 1) / a * a; }
 
 struct Layout {
     size_t img_planes, inst_planes, masks, dev_inst, ist, tiles, tile_inst, ring, lambdas, flows,
-        globals, staging, img_flags, inst_flags, trace, total;
+        globals, staging, img_flags, inst_flags, scratch, trace, total;
     size_t ring_cap;
     size_t max_tiles;
     size_t max_hw;
@@ -93,6 +93,7 @@ Layout make_layout(const pmf_batch_desc *d) {
     L.staging = take(sizeof(int32_t) * 3 * L.max_hw);
     L.img_flags = take(sizeof(int32_t) * d->n_images);
     L.inst_flags = take(sizeof(int32_t) * d->n_inst);
+    L.scratch = take(256);                        // small device results (status words)
     L.trace = take(sizeof(TraceEvent) * TRACE_CAP);
     L.total = off;
     return L;
@@ -691,6 +692,24 @@ pmf_status pmf_get_flows(pmf_batch *b, int32_t inst, int64_t *flows) {
     if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->last_n_lambda) return PMF_ERR_NOT_READY;
     for (int k = 0; k < b->last_n_lambda; ++k) flows[k] = b->flows_h[(size_t)inst * b->desc.max_lambdas + k];
     return PMF_OK;
+}
+
+pmf_status pmf_get_flow_arcs(pmf_batch *b, int32_t inst, int32_t *f_h, int32_t *f_v, int32_t *f_s,
+                             int32_t *f_t) {
+    if (!b || !f_h || !f_v || !f_s || !f_t || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
+    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
+    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->last_n_lambda) return PMF_ERR_NOT_READY;
+    DeviceGuard dg(b->device);
+    const DevInst &d = b->dinst[inst];
+    const int lambda = b->lam_h[(size_t)inst * b->desc.max_lambdas + b->last_n_lambda - 1];
+    int32_t *status_d = (int32_t *)(b->ws + b->L.scratch);
+    cudaStream_t s = b->cap_stream;
+    cudaError_t e = launch_return_excess(b->P, d, lambda, 1 << 17, f_h, f_v, f_s, f_t, status_d, s);
+    int32_t status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, status_d, sizeof(status), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(e);
+    return status == 0 ? PMF_OK : PMF_ERR_NOT_CONVERGED;
 }
 
 pmf_status pmf_get_timing(pmf_batch *b, float *solve_ms, float *worker_ms) {

@@ -138,6 +138,9 @@ cudaError_t launch_reset(const Params &P, cudaStream_t s);
 cudaError_t launch_init(const Params &P, int max_pixels, cudaStream_t s);
 cudaError_t launch_worker(const Params &P, int grid, cudaStream_t s);
 cudaError_t launch_begin_round(const Params &P, cudaStream_t s);
+cudaError_t launch_return_excess(const Params &P, const DevInst &d, int lambda, int max_sweeps,
+                                 int32_t *f_h, int32_t *f_v, int32_t *f_s, int32_t *f_t, int32_t *status,
+                                 cudaStream_t s);
 int worker_warps_per_block();
 cudaError_t worker_occupancy(int tile_h, int *blocks_per_sm);
 

@@ -1376,6 +1376,98 @@ cudaError_t launch_init(const Params &P, int max_pixels, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// --------------------------------------------------------------------------
+// per-arc flow of a solved instance (phase 2 of push-relabel): the solve
+// leaves a maximum preflow whose excess sits on pixels that cannot reach t;
+// returning that excess to s turns it into a feasible maximum flow of the
+// same value (Section 2's flow, arc by arc)
+// --------------------------------------------------------------------------
+constexpr int RETURN_THREADS = 1024;
+
+// One block.  Start: the preflow with every source arc carrying cs(p) and
+// every sink arc ct(p) - rt(p); a pixel's excess is its inflow minus its
+// outflow.  Sweep: a pixel with excess first sends it back along its own
+// source arc, then back along the pair arcs that carry flow into it (each push
+// lowers a positive flow towards zero).  Only a pair's receiving end ever
+// changes its flow, and no flow changes sign, so the two ends never act on one
+// pair at once.  Every push lowers the sum of |flows| by its amount, so the
+// loop ends; it stops when a whole sweep saw no excess.  The sink arcs never
+// change: the value stays the flow into t.
+__global__ void __launch_bounds__(RETURN_THREADS) return_excess_kernel(
+    const int32_t *E, const int32_t *RT, const int32_t *FR, const int32_t *FD, const int32_t *SRC0,
+    const int32_t *SLOPE, const int32_t *CT, int lambda, int H, int W, int pitch, int max_sweeps,
+    int32_t *f_h, int32_t *f_v, int32_t *f_s, int32_t *f_t, int32_t *status) {
+    const int n = H * W;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int y = p / W, x = p - y * W;
+        const size_t i = (size_t)y * pitch + x;
+        f_h[p] = x < W - 1 ? FR[i] : 0;
+        f_v[p] = y < H - 1 ? FD[i] : 0;
+        f_s[p] = SRC0[i] + SLOPE[i] * lambda;
+        f_t[p] = E[i];                      // the excess, until the last step
+    }
+    __syncthreads();
+    volatile int32_t *vh = f_h, *vv = f_v, *vs = f_s, *ve = f_t;
+    int sweeps = 0;
+    bool more = true;
+    while (more && sweeps < max_sweeps) {
+        bool any = false;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int ex = ve[p];
+            if (ex <= 0) continue;
+            any = true;
+            const int y = p / W, x = p - y * W;
+            int rem = ex;
+            const int r0 = min(rem, (int)vs[p]);        // back to s
+            vs[p] = vs[p] - r0;
+            rem -= r0;
+            if (rem > 0 && x > 0) {                     // flow arriving from the left
+                const int f = vh[p - 1];
+                const int d = f > 0 ? min(rem, f) : 0;
+                if (d) { vh[p - 1] = f - d; atomicAdd(&f_t[p - 1], d); rem -= d; }
+            }
+            if (rem > 0 && x < W - 1) {                 // from the right
+                const int f = -vh[p];
+                const int d = f > 0 ? min(rem, f) : 0;
+                if (d) { vh[p] = -(f - d); atomicAdd(&f_t[p + 1], d); rem -= d; }
+            }
+            if (rem > 0 && y > 0) {                     // from above
+                const int f = vv[p - W];
+                const int d = f > 0 ? min(rem, f) : 0;
+                if (d) { vv[p - W] = f - d; atomicAdd(&f_t[p - W], d); rem -= d; }
+            }
+            if (rem > 0 && y < H - 1) {                 // from below
+                const int f = -vv[p];
+                const int d = f > 0 ? min(rem, f) : 0;
+                if (d) { vv[p] = -(f - d); atomicAdd(&f_t[p + W], d); rem -= d; }
+            }
+            if (ex - rem) atomicSub(&f_t[p], ex - rem);
+        }
+        ++sweeps;
+        more = __syncthreads_or(any) != 0;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int y = p / W, x = p - y * W;
+        const size_t i = (size_t)y * pitch + x;
+        f_t[p] = CT[i] - RT[i];
+    }
+    if (threadIdx.x == 0) *status = more ? 1 : 0;
+}
+
+cudaError_t launch_return_excess(const Params &P, const DevInst &d, int lambda, int max_sweeps,
+                                 int32_t *f_h, int32_t *f_v, int32_t *f_s, int32_t *f_t, int32_t *status,
+                                 cudaStream_t s) {
+    const size_t PS = (size_t)d.rows * d.pitch;
+    const int32_t *base = P.planes + d.plane_off;
+    (void)cudaGetLastError();
+    return_excess_kernel<<<1, RETURN_THREADS, 0, s>>>(base + P_E * PS, base + P_RT * PS, base + P_FR * PS,
+                                                      base + P_FD * PS, base + P_SRC0 * PS, base + P_SLOPE * PS,
+                                                      base + P_CT * PS, lambda, d.H, d.W, d.pitch, max_sweeps,
+                                                      f_h, f_v, f_s, f_t, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_worker(const Params &P, int grid, cudaStream_t s) {
     (void)cudaGetLastError();
     if (P.tile_h == 4) worker_kernel<4><<<grid, WORKER_WARPS * 32, 0, s>>>(P);

@@ -39,7 +39,7 @@ EXPORTS = ["pmf_workspace_size", "pmf_create_batch", "pmf_set_tuning", "pmf_get_
            "pmf_get_cut", "pmf_get_flow", "pmf_get_cuts", "pmf_get_flows", "pmf_get_timing",
            "pmf_get_stats", "pmf_get_trace", "pmf_get_profile", "pmf_get_mask_layout",
            "pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error",
-           "pmf_solve_noalloc"]
+           "pmf_solve_noalloc", "pmf_get_flow_arcs"]
 
 
 class PmfError(RuntimeError):
@@ -116,6 +116,7 @@ def lib(path: str | None = None):
             L.pmf_get_stats.argtypes = [vp, i32, ctypes.POINTER(Stats)]
             L.pmf_get_cuts.argtypes = [vp, i32, vp, ctypes.c_int]
             L.pmf_get_flows.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64)]
+            L.pmf_get_flow_arcs.argtypes = [vp, i32, vp, vp, vp, vp]
             L.pmf_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
             L.pmf_get_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
             L.pmf_get_trace.argtypes = [vp, ctypes.POINTER(TraceEvent), i32, i32p]
@@ -294,6 +295,18 @@ class Batch:
         _check(lib().pmf_get_flows(self._h, int(inst), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
                "pmf_get_flows")
         return out
+
+    def flow_arcs(self, inst: int) -> dict:
+        """A feasible maximum flow of the instance at its last lambda, per arc:
+        {"f_h", "f_v", "f_s", "f_t"} as int32 host arrays [H, W] (see
+        pmf_get_flow_arcs).  The arrays are computed in device memory."""
+        import torch
+        H, W = self.shapes[self.inst_image[inst]]
+        bufs = torch.empty((4, H, W), dtype=torch.int32, device=f"cuda:{self.device}")
+        ptr = [ctypes.c_void_p(bufs[j].data_ptr()) for j in range(4)]
+        _check(lib().pmf_get_flow_arcs(self._h, int(inst), *ptr), "pmf_get_flow_arcs")
+        a = bufs.cpu().numpy()
+        return {"f_h": a[0], "f_v": a[1], "f_s": a[2], "f_t": a[3]}
 
     def cuts(self, inst: int, out=None) -> np.ndarray:
         """All masks of an instance, [n_lambda, H, W] (numpy host array, or a
