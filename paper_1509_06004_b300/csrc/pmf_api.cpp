@@ -28,9 +28,10 @@ int round_up_i(int v, int a) { return (v + a - 1) / a * a; }
 
 struct Layout {
     size_t img_planes, inst_planes, masks, dev_inst, ist, tiles, tile_inst, ring, lambdas, flows,
-        globals, staging, img_flags, inst_flags, scratch, trace, total;
+        globals, staging, img_flags, inst_flags, scratch, trace, strip_cache, total;
     size_t ring_cap;
     size_t max_tiles;
+    size_t max_strips;                          // relabel strips (tile columns x 32-row bands)
     size_t max_hw;
     std::vector<int> rows, pitch;               // per image
     std::vector<int64_t> img_off;               // per image, int32 elements
@@ -65,6 +66,7 @@ Layout make_layout(const pmf_batch_desc *d) {
     L.mask_off.resize(d->n_inst);
     size_t inst_elems = 0, mask_bytes = 0;
     L.max_tiles = 0;
+    L.max_strips = 0;
     for (int i = 0; i < d->n_inst; ++i) {
         const int im = d->inst_image[i];
         const size_t ps = (size_t)L.rows[im] * L.pitch[im];
@@ -73,6 +75,7 @@ Layout make_layout(const pmf_batch_desc *d) {
         L.mask_off[i] = (int64_t)mask_bytes;
         mask_bytes += (size_t)d->max_lambdas * ps;
         L.max_tiles += (size_t)(L.rows[im] / 4) * ((d->img_w[im] + TILE_IN - 1) / TILE_IN);   // smallest tile height
+        L.max_strips += (size_t)((L.rows[im] + BFS_ROWS - 1) / BFS_ROWS) * ((d->img_w[im] + TILE_IN - 1) / TILE_IN);
     }
     // every tile can be queued once, and every resident warp may hold a ticket
     L.ring_cap = 1;
@@ -95,6 +98,7 @@ Layout make_layout(const pmf_batch_desc *d) {
     L.inst_flags = take(sizeof(int32_t) * d->n_inst);
     L.scratch = take(256);                        // small device results (status words)
     L.trace = take(sizeof(TraceEvent) * TRACE_CAP);
+    L.strip_cache = take(sizeof(int32_t) * STRIP_REC_WORDS * L.max_strips);
     L.total = off;
     return L;
 }
@@ -401,6 +405,7 @@ pmf_status pmf_create_batch(const pmf_batch_desc *desc, void *dev_workspace, siz
     P.tiles = (TileState *)(b->ws + L.tiles);
     P.tile_inst = (const int32_t *)(b->ws + L.tile_inst);
     P.ring = (int32_t *)(b->ws + L.ring);
+    P.strip_cache = (int32_t *)(b->ws + L.strip_cache);
     P.lambdas = (const int32_t *)(b->ws + L.lambdas);
     P.flows = (long long *)(b->ws + L.flows);
     P.g = (Globals *)(b->ws + L.globals);
@@ -419,7 +424,9 @@ pmf_status pmf_create_batch(const pmf_batch_desc *desc, void *dev_workspace, siz
     // not set stay zero), flags
     cudaStream_t s = b->setup_stream;
     e = cudaMemsetAsync(b->ws + L.img_planes, 0, L.masks - L.img_planes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->ws + L.img_flags, 0, L.total - L.img_flags, s);
+    // flags, scratch and trace start zeroed (the strip records after them are
+    // always written by a strip's first visit of an epoch before they are read)
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ws + L.img_flags, 0, L.strip_cache - L.img_flags, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->ws + L.globals, 0, sizeof(Globals), s);
     if (e == cudaSuccess) {
         const pmf_status st = refresh_geometry(b, s);

@@ -16,6 +16,8 @@ constexpr int TILE_IN = 30;                // interior columns of a tile: lanes 
 constexpr int ROW_ALIGN = 16;              // rows padded so tile heights 4/8/16 divide them
 constexpr int32_t HINF = 0x3fffffff;       // label of a pixel that cannot reach t
 constexpr int BFS_ROWS = 32;               // rows of a relabel strip (a column of tiles)
+// per relabel strip: 6 arc masks, 3 border residuals and 32 label rows, 32 lanes each
+constexpr int STRIP_REC_WORDS = (9 + BFS_ROWS) * 32;
 constexpr int N_INST_PLANES = 8;           // e, h, rt, fR, fD, src0, slope, ct
 constexpr int N_IMG_PLANES = 2;            // w_h, w_v
 enum Plane { P_E = 0, P_H = 1, P_RT = 2, P_FR = 3, P_FD = 4, P_SRC0 = 5, P_SLOPE = 6, P_CT = 7 };
@@ -114,6 +116,7 @@ struct Params {
     TileState *tiles;
     const int32_t *tile_inst;
     int32_t *ring;
+    int32_t *strip_cache;        // [relabel strips][STRIP_REC_WORDS]
     const int32_t *lambdas;      // [n_inst][max_lambdas]
     long long *flows;            // [n_inst][max_lambdas]
     Globals *g;

@@ -848,8 +848,55 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     if (lane == 31) vX = T.tx < D.tiles_x - 1 && ldv(&P.tiles[g + 1].epoch) == epoch;
     __threadfence();
 
+    // This strip's record: the arc bit masks and border residuals its first
+    // visit of the epoch found (arcs do not change during a relabel phase),
+    // and its labels as its last visit left them.  Words [k][lane]:
+    // k = 0..5 masks R, D, U, E, Q, V; 6..8 residuals up from row 0, down
+    // into row 0, up into the last row; 9 + i the label of row i.
+    int32_t *REC = P.strip_cache + (size_t)(D.lead_base + (T.ty / SPAN) * D.tiles_x + T.tx) * STRIP_REC_WORDS;
+    int(*Dl)[33] = S.d;
+    unsigned bR = 0, bD = 0, bU = 0, bE = 0, bQ = 0, bV = 0;
+    int hT = HINF, res_up0 = 0, res_down_above = 0, res_up_last = 0, dold_top = HINF, dold_bot = HINF;
+    const bool below = T.y0 + BR < D.rows;
+    int hB = HINF;
+    if (own && vB && below) hB = __ldcg(Hh + (size_t)(T.y0 + BR) * pitch + T.X);
+    if (own_valid) {
+        // a second visit in this epoch: masks and residuals from the record,
+        // labels of this strip's own columns from the record, the ghost
+        // columns' from the neighbouring strips' labels
+        bR = (unsigned)__ldcg(REC + 0 * 32 + lane);
+        bD = (unsigned)__ldcg(REC + 1 * 32 + lane);
+        bU = (unsigned)__ldcg(REC + 2 * 32 + lane);
+        bE = (unsigned)__ldcg(REC + 3 * 32 + lane);
+        bQ = (unsigned)__ldcg(REC + 4 * 32 + lane);
+        bV = (unsigned)__ldcg(REC + 5 * 32 + lane);
+        res_up0 = __ldcg(REC + 6 * 32 + lane);
+        res_down_above = __ldcg(REC + 7 * 32 + lane);
+        res_up_last = __ldcg(REC + 8 * 32 + lane);
+        if (own && T.y0 > 0 && vT) hT = __ldcg(Hh + (size_t)(T.y0 - 1) * pitch + T.X);
+        constexpr int LH = 16;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BR; c0 += LH) {
+            int dv[LH];
+#pragma unroll
+            for (int j = 0; j < LH; ++j) {
+                const int i = c0 + j;
+                const bool rowok = T.y0 + i < D.rows;
+                dv[j] = own ? __ldcg(REC + (9 + i) * 32 + lane)
+                            : (T.inb && rowok && vX) ? __ldcg(Hh + (size_t)(T.y0 + i) * pitch + T.X) : HINF;
+            }
+#pragma unroll
+            for (int j = 0; j < LH; ++j) {
+                const int i = c0 + j;
+                if (i == 0) dold_top = dv[j];
+                if (i == BR - 1) dold_bot = dv[j];
+                Dl[i][lane] = dv[j];
+                if (lane == 1) S.dl0[0][i] = dv[j];
+                if (lane == 30) S.dl0[1][i] = dv[j];
+            }
+        }
+    } else {
     // the row above the strip: residual of the arcs up and down across the border
-    int hT = HINF, res_up0 = 0, res_down_above = 0;
     if (own && T.y0 > 0) {
         const size_t j = (size_t)(T.y0 - 1) * pitch + T.X;
         const int wvT = __ldg(WV + j), fdT = __ldcg(FD + j);
@@ -857,18 +904,13 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
         res_down_above = wvT - fdT;   // above -> row 0
         if (vT) hT = __ldcg(Hh + j);
     }
-    const bool below = T.y0 + BR < D.rows;
-    int hB = HINF;
-    if (own && vB && below) hB = __ldcg(Hh + (size_t)(T.y0 + BR) * pitch + T.X);
 
     // residual arcs as bit masks (bit i = row i): R/L/D/U = from the pixel to
     // that neighbour; E = positive excess; Q = arc from this column to the one
     // on its right (read by lane 1 from ghost lane 0); V = arc from the right
     // neighbour into this column (used by lane 30).  Labels live in this
     // lane's own column of the warp's shared memory.
-    int(*Dl)[33] = S.d;
-    unsigned bR = 0, bD = 0, bU = 0, bE = 0, bQ = 0, bV = 0;
-    int prev_up = res_up0, res_up_last = 0, dold_top = HINF, dold_bot = HINF;
+    int prev_up = res_up0;
     // 4 rows at a time: every global load of a batch is issued before any of
     // its results is used or written to shared memory, so a batch costs one
     // memory round trip instead of one per row
@@ -912,6 +954,17 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
             if (lane == 1) S.dl0[0][i] = dv[j];
             if (lane == 30) S.dl0[1][i] = dv[j];
         }
+    }
+    // the record's masks and residuals for the epoch's later visits
+    __stcg(REC + 0 * 32 + lane, (int)bR);
+    __stcg(REC + 1 * 32 + lane, (int)bD);
+    __stcg(REC + 2 * 32 + lane, (int)bU);
+    __stcg(REC + 3 * 32 + lane, (int)bE);
+    __stcg(REC + 4 * 32 + lane, (int)bQ);
+    __stcg(REC + 5 * 32 + lane, (int)bV);
+    __stcg(REC + 6 * 32 + lane, res_up0);
+    __stcg(REC + 7 * 32 + lane, res_down_above);
+    __stcg(REC + 8 * 32 + lane, res_up_last);
     }
     // arcs from this column to the one on its left: the left column's
     // residual w + f towards it (bV of the lane on the left)
@@ -1038,6 +1091,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
             M[idx] = di >= HINF ? 1 : 0;
             dm = di < HINF ? max(dm, di) : dm;
         }
+        if (own) __stcg(REC + (9 + i) * 32 + lane, di);
         live |= di < HINF ? (1u << i) : 0u;
     }
     // active pixels (positive excess, finite label) of each member tile

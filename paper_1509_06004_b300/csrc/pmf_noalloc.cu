@@ -86,6 +86,8 @@ extern "C" PMF_API pmf_status pmf_solve_noalloc(int32_t H, int32_t W, const int3
     const size_t o_flows = take(sizeof(int64_t) * n_lambda);
     const size_t o_glob = take(sizeof(Globals));
     const size_t o_flags = take(sizeof(int32_t) * 2);
+    const size_t n_strips = (size_t)tiles_x * ((rows + BFS_ROWS - 1) / BFS_ROWS);
+    const size_t o_strips = take(sizeof(int32_t) * STRIP_REC_WORDS * n_strips);
     if (off > kScratchBytes) return PMF_ERR_OUT_OF_MEMORY;
 
     std::lock_guard<std::mutex> guard(g_lock);
@@ -125,6 +127,7 @@ extern "C" PMF_API pmf_status pmf_solve_noalloc(int32_t H, int32_t W, const int3
     P.tiles = reinterpret_cast<TileState *>(ws + o_tiles);
     P.tile_inst = reinterpret_cast<const int32_t *>(ws + o_tinst);
     P.ring = reinterpret_cast<int32_t *>(ws + o_ring);
+    P.strip_cache = reinterpret_cast<int32_t *>(ws + o_strips);
     P.lambdas = reinterpret_cast<const int32_t *>(ws + o_lam);
     P.flows = reinterpret_cast<long long *>(ws + o_flows);
     P.g = reinterpret_cast<Globals *>(ws + o_glob);
