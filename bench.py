@@ -403,8 +403,8 @@ def serving_bench(args, dev):
     out = {"rate_per_s": args.serving_rate, "requests": len(reqs), "max_side": args.serving_max_side,
            "budget_bytes": args.serving_budget, "pixel_solves": sum(r.workload.pixel_solves for r in reqs)}
     for name, slots in (("continuous", args.serving_slots), ("one_at_a_time", 1)):
-        serving.serve(warm, slots=slots, budget_bytes=args.serving_budget, device=dev.index, segments=5)
-        st = serving.serve(reqs, slots=slots, budget_bytes=args.serving_budget, device=dev.index, segments=5)
+        serving.serve(warm, slots=slots, budget_bytes=args.serving_budget, device=dev.index)
+        st = serving.serve(reqs, slots=slots, budget_bytes=args.serving_budget, device=dev.index)
         out[name] = st.summary()
         out[name]["slots"] = slots
         torch.cuda.empty_cache()

@@ -427,9 +427,11 @@ __device__ int finish(const Params &P, int g, int inst, int phase, bool requeue,
     unsigned long long base = 0;
     if (lane == 0) {
         const int delta = k - 1;
-        if (delta != 0) {
+        if (delta < 0) {                 // the count can only reach zero when it falls
             const int old = atomicAdd(&P.ist[inst].outstanding, delta);
             trans = (old + delta == 0);
+        } else if (delta > 0) {          // no result needed: a reduction, no round trip
+            atomicAdd(&P.ist[inst].outstanding, delta);
         }
         if (kq) {
             __threadfence();
