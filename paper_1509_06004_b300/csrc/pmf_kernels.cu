@@ -614,49 +614,75 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
             // pixel's outflow.  a is clamped at 2^29: residuals are below
             // 2^29, so a larger a never changes the result.
             constexpr int ACL = 1 << 29;
+            // all rows scan in step (independent shuffles overlap); a direction
+            // is skipped when no pixel of the tile can send anything along it
+            {                                          // rightwards
+                int A[TH], B[TH];
+                bool go = false;
 #pragma unroll
-            for (int i = 0; i < TH; ++i) {             // rightwards
-                const int hR = __shfl_down_sync(FULL_MASK, h[i], 1);
-                const int rR = wh[i] - fr[i];
-                const bool live = own && h[i] < HINF;
-                int A = live ? min(e[i], ACL) : 0;
-                int B = (live && rR > 0 && hR < h[i]) ? rR : 0;
-                if (!__any_sync(FULL_MASK, A > 0 && B > 0)) continue;
+                for (int i = 0; i < TH; ++i) {
+                    const int hR = __shfl_down_sync(FULL_MASK, h[i], 1);
+                    const int rR = wh[i] - fr[i];
+                    const bool live = own && h[i] < HINF;
+                    A[i] = live ? min(e[i], ACL) : 0;
+                    B[i] = (live && rR > 0 && hR < h[i]) ? rR : 0;
+                    go |= A[i] > 0 && B[i] > 0;
+                }
+                if (__any_sync(FULL_MASK, go)) {
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int A2 = __shfl_up_sync(FULL_MASK, A, o);
-                    const int B2 = __shfl_up_sync(FULL_MASK, B, o);
-                    if (lane >= o) {
-                        B = min(A + B2, B);
-                        A = min(A2 + A, ACL);
+                    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                        for (int i = 0; i < TH; ++i) {
+                            const int A2 = __shfl_up_sync(FULL_MASK, A[i], o);
+                            const int B2 = __shfl_up_sync(FULL_MASK, B[i], o);
+                            if (lane >= o) {
+                                B[i] = min(A[i] + B2, B[i]);
+                                A[i] = min(A2 + A[i], ACL);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < TH; ++i) {
+                        const int out = min(A[i], B[i]);
+                        const int in = __shfl_up_sync(FULL_MASK, out, 1);
+                        e[i] += (lane > 0 ? in : 0) - out;
+                        fr[i] += out;
                     }
                 }
-                const int out = min(A, B);
-                const int in = __shfl_up_sync(FULL_MASK, out, 1);
-                e[i] += (lane > 0 ? in : 0) - out;
-                fr[i] += out;
             }
+            {                                          // leftwards
+                int A[TH], B[TH];
+                bool go = false;
 #pragma unroll
-            for (int i = 0; i < TH; ++i) {             // leftwards
-                const int hL = __shfl_up_sync(FULL_MASK, h[i], 1);
-                const int rL = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
-                const bool live = own && h[i] < HINF;
-                int A = live ? min(e[i], ACL) : 0;
-                int B = (live && rL > 0 && hL < h[i]) ? rL : 0;
-                if (!__any_sync(FULL_MASK, A > 0 && B > 0)) continue;
+                for (int i = 0; i < TH; ++i) {
+                    const int hL = __shfl_up_sync(FULL_MASK, h[i], 1);
+                    const int rL = __shfl_up_sync(FULL_MASK, wh[i] + fr[i], 1);
+                    const bool live = own && h[i] < HINF;
+                    A[i] = live ? min(e[i], ACL) : 0;
+                    B[i] = (live && rL > 0 && hL < h[i]) ? rL : 0;
+                    go |= A[i] > 0 && B[i] > 0;
+                }
+                if (__any_sync(FULL_MASK, go)) {
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int A2 = __shfl_down_sync(FULL_MASK, A, o);
-                    const int B2 = __shfl_down_sync(FULL_MASK, B, o);
-                    if (lane + o < 32) {
-                        B = min(A + B2, B);
-                        A = min(A2 + A, ACL);
+                    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                        for (int i = 0; i < TH; ++i) {
+                            const int A2 = __shfl_down_sync(FULL_MASK, A[i], o);
+                            const int B2 = __shfl_down_sync(FULL_MASK, B[i], o);
+                            if (lane + o < 32) {
+                                B[i] = min(A[i] + B2, B[i]);
+                                A[i] = min(A2 + A[i], ACL);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < TH; ++i) {
+                        const int out = min(A[i], B[i]);
+                        const int in = __shfl_down_sync(FULL_MASK, out, 1);
+                        e[i] += (lane < 31 ? in : 0) - out;
+                        fr[i] -= (lane < 31 ? in : 0);
                     }
                 }
-                const int out = min(A, B);
-                const int in = __shfl_down_sync(FULL_MASK, out, 1);
-                e[i] += (lane < 31 ? in : 0) - out;
-                fr[i] -= (lane < 31 ? in : 0);
             }
         } else {
             int dDa[TH], dUa[TH];
