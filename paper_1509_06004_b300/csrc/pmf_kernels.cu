@@ -484,7 +484,7 @@ __device__ __forceinline__ TileGeo tile_geo(int g, const DevInst &D, int TH) {
 // push/relabel visit of one tile (Goldberg-Tarjan push and relabel operations,
 // the solver the paper runs through NPPI, Section 3)
 // --------------------------------------------------------------------------
-template <int TH>
+template <int TH, int PO>
 __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, const DevInst &D,
                          int kcur, bool &self_active, unsigned &nbmask) {
     const TileGeo T = tile_geo(g, D, TH);
@@ -575,7 +575,7 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
         // during the push phase, so the two ends of an edge never push
         // against each other.  Push phase: an active pixel sends excess to t
         // first, then to lower neighbours along residual arcs.
-        if (P.chain_push) {
+        if constexpr (PO == 1) {
             // Chain order: excess may move on in the same sweep after it
             // arrives.  Every push is still along a residual arc to a lower
             // neighbour from a pixel holding the excess it sends, so this is
@@ -1166,7 +1166,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
 // --------------------------------------------------------------------------
 constexpr int WORKER_WARPS = 4;
 
-template <int TH>
+template <int TH, int PO>
 // at least 4 resident blocks per SM at tile height 4 (128 registers) and 2 at
 // height 8: with fewer, throughput-bound batches lose more than the spills cost
 __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_kernel(const __grid_constant__ Params P) {
@@ -1218,7 +1218,7 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_ker
         // push/relabel item outlived its phase, which the phase changes rule out
         const bool stray = phase == PH_BFS && ((g - D.tile_base) / D.tiles_x) % (BFS_ROWS / TH) != 0;
         if (stray && lane == 0) atomicOr(&P.g->err, GE_PHASE);
-        if (status == PMF_OK && phase == PH_PR) pr_visit<TH>(P, S, g, inst, D, k, requeue, nb);
+        if (status == PMF_OK && phase == PH_PR) pr_visit<TH, PO>(P, S, g, inst, D, k, requeue, nb);
         else if (status == PMF_OK && phase == PH_BFS && !stray)
             bfs_visit<TH>(P, S, g, inst, D, epoch, k, requeue, nb);
         __threadfence();
@@ -1552,8 +1552,14 @@ cudaError_t launch_return_excess(const Params &P, const DevInst &d, int lambda, 
 
 cudaError_t launch_worker(const Params &P, int grid, cudaStream_t s) {
     (void)cudaGetLastError();
-    if (P.tile_h == 4) worker_kernel<4><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
-    else worker_kernel<8><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
+    // one kernel per tile height and push order: each holds only the sweep it runs
+    if (P.tile_h == 4) {
+        if (P.chain_push) worker_kernel<4, 1><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
+        else worker_kernel<4, 0><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
+    } else {
+        if (P.chain_push) worker_kernel<8, 1><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
+        else worker_kernel<8, 0><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
+    }
     return cudaGetLastError();
 }
 
@@ -1567,8 +1573,8 @@ int worker_warps_per_block() { return WORKER_WARPS; }
 
 cudaError_t worker_occupancy(int tile_h, int *blocks_per_sm) {
     if (tile_h == 4)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<4>, WORKER_WARPS * 32, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<8>, WORKER_WARPS * 32, 0);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<4, 0>, WORKER_WARPS * 32, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<8, 0>, WORKER_WARPS * 32, 0);
 }
 
 }  // namespace pmf
