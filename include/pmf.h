@@ -168,6 +168,22 @@ PMF_API pmf_status pmf_set_capacities(pmf_batch *b, int32_t image, const int32_t
 PMF_API pmf_status pmf_set_terminals(pmf_batch *b, int32_t inst, const int32_t *src0,
                              const int32_t *slope, const int32_t *sink, int on_device);
 
+/* Section 3.2's s-t swap: the caller may solve an instance with s and t
+ * exchanged, passing its sink capacities as src0 (slope 0) and its source
+ * capacities at one lambda as sink through pmf_set_terminals (pairwise
+ * capacities are symmetric, so the exchanged problem is the same grid).
+ * rule = 1 tells the solver so: the flow value is unchanged, and the mask
+ * pmf_get_cut(s) returns is the ORIGINAL problem's maximal source set, i.e.
+ * the complement of the exchanged problem's minimal source set.  The GPU finds
+ * that set after each certified step as the pixels reachable in the residual
+ * graph from pixels holding excess (every minimum cut's source side contains
+ * them, and they form one).  rule = 0 (default): the maximal source set of the
+ * problem as given.  Takes effect at the next pmf_solve_schedule.  With rule 1
+ * the sink capacities do not follow lambda, so a schedule of one lambda is the
+ * intended use (a warm-started exchanged schedule would need falling sink
+ * capacities).  PMF_ERR_INVALID_ARG for a bad instance or rule. */
+PMF_API pmf_status pmf_set_cut_rule(pmf_batch *b, int32_t inst, int32_t rule);
+
 /* Solve every instance at every lambda of its schedule.  lambdas is a host
  * array [n_inst][n_lambda] (n_lambda <= max_lambdas), nondecreasing along each
  * row (else PMF_ERR_NOT_MONOTONE, nothing launched).  Asynchronous on

@@ -228,6 +228,53 @@ def brute_force_graph(n: int, tail, head, cap, s: int, t: int):
     return best, union, len(arg)
 
 
+def brute_force_min_source_set(n: int, tail, head, cap, s: int, t: int):
+    """The intersection of every minimising s side (the minimal source set of
+    a minimum cut) of a digraph with at most 16 non-terminal nodes, by
+    enumeration: uint8 vector over nodes."""
+    others = [u for u in range(n) if u != s and u != t]
+    k = len(others)
+    assert k <= 16, "brute force is limited to 16 non-terminal nodes"
+    subsets = np.arange(1 << k, dtype=np.int64)
+    side = np.zeros((n, 1 << k), dtype=np.int64)
+    side[s, :] = 1
+    for bit, u in enumerate(others):
+        side[u, :] = (subsets >> bit) & 1
+    cost = np.zeros(1 << k, dtype=np.int64)
+    for u, v, c in zip(np.asarray(tail), np.asarray(head), np.asarray(cap, np.int64)):
+        if c:
+            cost += c * side[u] * (1 - side[v])
+    arg = np.nonzero(cost == cost.min())[0]
+    inter = np.zeros(n, np.uint8)
+    for bit, u in enumerate(others):
+        inter[u] = 1 if np.all((arg >> bit) & 1) else 0
+    inter[s] = 1
+    return inter
+
+
+def source_reach(n: int, tail, head, cap, flow, s: int):
+    """Nodes reachable from s in the residual graph of a flow (residual of an
+    arc u->v: cap - flow; of its reverse v->u: flow).  For a maximum flow this
+    is the minimal source set of a minimum cut (Ford-Fulkerson)."""
+    adj = [[] for _ in range(n)]
+    for u, v, c, f in zip(np.asarray(tail).tolist(), np.asarray(head).tolist(),
+                          np.asarray(cap, np.int64).tolist(), np.asarray(flow, np.int64).tolist()):
+        if c - f > 0:
+            adj[u].append(v)
+        if f > 0:
+            adj[v].append(u)
+    seen = np.zeros(n, np.uint8)
+    seen[s] = 1
+    stack = [s]
+    while stack:
+        u = stack.pop()
+        for v in adj[u]:
+            if not seen[v]:
+                seen[v] = 1
+                stack.append(v)
+    return seen
+
+
 def brute_force_grid(H, W, w_h, w_v, src0, slope, sink, lam):
     """Brute-force min cut of a grid instance with H*W <= 16, its cut cost
     written straight from the definition of Section 2 (pairwise edges counted

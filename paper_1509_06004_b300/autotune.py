@@ -81,7 +81,7 @@ def cached(wl, device: int = 0, path: str = CACHE_PATH) -> dict | None:
     return load_cache(path).get(f"{gpu_name(device)}|{workload_class(wl)}")
 
 
-def gpu_measure(wl, segments: int, knobs: dict, reps: int = 2, device: int = 0) -> float:
+def gpu_measure(wl, segments: int, knobs: dict, reps: int = 3, device: int = 0) -> float:
     """Median device time (ms) of ``reps`` solves (after one warm-up) of the
     workload cut into ``segments`` pieces per seed."""
     import torch
@@ -104,7 +104,7 @@ def gpu_measure(wl, segments: int, knobs: dict, reps: int = 2, device: int = 0) 
     return float(np.median(ts))
 
 
-def tune(wl, measure=None, budget_s: float = 90.0, reps: int = 2, log=None) -> dict:
+def tune(wl, measure=None, budget_s: float = 90.0, reps: int = 3, log=None) -> dict:
     """Coordinate descent over ``segments`` then each knob of SPACE, starting
     from DEFAULTS; stops when a full pass brings no gain or the time budget is
     spent.  ``measure(wl, segments, knobs) -> ms`` defaults to gpu_measure.
@@ -148,7 +148,7 @@ def tune(wl, measure=None, budget_s: float = 90.0, reps: int = 2, log=None) -> d
 
 
 def tune_and_cache(wl, device: int = 0, budget_s: float = 90.0, path: str = CACHE_PATH, log=None) -> dict:
-    res = tune(wl, measure=lambda w, s, k: gpu_measure(w, s, k, device=device), budget_s=budget_s, log=log)
+    res = tune(wl, measure=lambda w, s, k: gpu_measure(w, s, k, reps=3, device=device), budget_s=budget_s, log=log)
     cache = load_cache(path)
     res["class"] = workload_class(wl)
     cache[f"{gpu_name(device)}|{workload_class(wl)}"] = res

@@ -502,6 +502,19 @@ pmf_status pmf_set_capacities(pmf_batch *b, int32_t image, const int32_t *w_h, c
     return cuda_err(e);
 }
 
+pmf_status pmf_set_cut_rule(pmf_batch *b, int32_t inst, int32_t rule) {
+    if (!b || inst < 0 || inst >= b->desc.n_inst || (rule != 0 && rule != 1)) return PMF_ERR_INVALID_ARG;
+    DeviceGuard dg(b->device);
+    if (b->in_flight) { cudaEventSynchronize(b->done); b->in_flight = false; }
+    b->dinst[inst].cut_rule = rule;
+    b->dinst_h[inst].cut_rule = rule;
+    cudaStream_t s = b->setup_stream;
+    cudaError_t e = cudaMemcpyAsync(b->ws + b->L.dev_inst + sizeof(DevInst) * inst, &b->dinst_h[inst],
+                                    sizeof(DevInst), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_err(e);
+}
+
 pmf_status pmf_set_terminals(pmf_batch *b, int32_t inst, const int32_t *src0, const int32_t *slope,
                              const int32_t *sink, int on_device) {
     if (!b || !src0 || !slope || !sink || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;

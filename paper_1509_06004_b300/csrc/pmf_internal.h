@@ -23,7 +23,9 @@ constexpr int N_IMG_PLANES = 2;            // w_h, w_v
 enum Plane { P_E = 0, P_H = 1, P_RT = 2, P_FR = 3, P_FD = 4, P_SRC0 = 5, P_SLOPE = 6, P_CT = 7 };
 
 // instance phases
-enum Phase { PH_BFS = 0, PH_PR = 1, PH_DONE = 2 };
+// PH_FWD: after a certified step of an instance whose caller swapped s and t,
+// the pass that finds the pixels reachable from excess (its cut)
+enum Phase { PH_BFS = 0, PH_PR = 1, PH_DONE = 2, PH_FWD = 3 };
 // tile queue states
 enum TState { T_IDLE = 0, T_QUEUED = 1, T_RUNNING = 2, T_DIRTY = 3 };
 // global error flags; GE_INTERNAL_MASK marks a broken scheduler invariant, after
@@ -45,7 +47,7 @@ struct DevInst {                 // read-only during a solve
     int64_t img_off;             // int32 elements from the image-plane base
     int64_t mask_off;            // bytes from the mask base
     int32_t n_leads;             // relabel strips (tiles_x * ceil(tiles_y / strip_span))
-    int32_t pad2_;               // keeps the size a multiple of 16 bytes
+    int32_t cut_rule;            // 0: maximal source set; 1: s and t swapped by the caller (pmf_set_cut_rule)
 };
 
 // 16-byte aligned: the worker reads the first four fields with one 16-byte

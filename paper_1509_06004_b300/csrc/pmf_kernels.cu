@@ -285,11 +285,18 @@ __device__ bool transition_once(const Params &P, int inst) {
             S->want_bfs = 0;
             mode = 1;
             trace(P, inst, TR_BFS_START, S);
-        } else if (phase == PH_BFS) {
+        } else if (phase == PH_BFS && S->active == 0 && D.cut_rule == 1) {
+            // certified, and the caller swapped s and t: the flow value is
+            // final; the cut comes from a forward pass over the strips
+            P.flows[(size_t)inst * P.max_lambdas + S->k] = (long long)S->flow;
+            S->epoch = S->epoch + 1;
+            S->phase = PH_FWD;
+            mode = 1;
+        } else if (phase == PH_BFS || phase == PH_FWD) {
             const unsigned long long visits = S->pr_visits + S->bfs_visits;
-            if (S->active == 0) {              // lambda step certified: record, advance
+            if (phase == PH_FWD || S->active == 0) {   // lambda step certified: record, advance
                 const int k = S->k;
-                P.flows[(size_t)inst * P.max_lambdas + k] = (long long)S->flow;
+                if (phase == PH_BFS) P.flows[(size_t)inst * P.max_lambdas + k] = (long long)S->flow;
                 S->k = k + 1;
                 S->step_mark = visits;
                 trace(P, inst, TR_STEP_DONE, S);
@@ -342,8 +349,9 @@ __device__ bool transition_once(const Params &P, int inst) {
     if (lane == 0) atomicAdd(&P.ist[inst].outstanding, 1);
     __threadfence();
     __syncwarp();
-    // a relabel works on strips (their leader tiles are queued); push/relabel on tiles
-    enqueue_tiles(P, inst, D, mode == 2, S->phase == PH_BFS);
+    // a relabel or forward pass works on strips (their leader tiles are
+    // queued); push/relabel on tiles
+    enqueue_tiles(P, inst, D, mode == 2, S->phase == PH_BFS || S->phase == PH_FWD);
     int last = 0;
     if (lane == 0) {
         __threadfence();
@@ -378,7 +386,7 @@ __device__ int finish(const Params &P, int g, int inst, int phase, bool requeue,
     volatile InstState *IS = P.ist + inst;
     bool allow = false;
     if (IS->status == PMF_OK) {
-        if (phase == PH_BFS) allow = true;
+        if (phase == PH_BFS || phase == PH_FWD) allow = true;
         else if (phase == PH_PR) allow = (IS->want_bfs == 0);
     }
     int item = -1;
@@ -386,7 +394,7 @@ __device__ int finish(const Params &P, int g, int inst, int phase, bool requeue,
         const int lt = g - D.tile_base;
         const int ty = lt / D.tiles_x, tx = lt - ty * D.tiles_x;
         int t = -1;
-        const int vs = (phase == PH_BFS) ? BFS_ROWS / P.tile_h : 1;   // strips in a relabel
+        const int vs = (phase == PH_BFS || phase == PH_FWD) ? BFS_ROWS / P.tile_h : 1;   // strips
         if (lane == 0 && ty >= vs) t = g - vs * D.tiles_x;
         if (lane == 1 && ty + vs < D.tiles_y) t = g + vs * D.tiles_x;
         if (lane == 2 && tx > 0) t = g - 1;
@@ -846,7 +854,7 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
 // the current lambda (1 = cannot reach t = source side) and each member tile's
 // count of active pixels for the push/relabel phase that may follow.
 // --------------------------------------------------------------------------
-template <int TH>
+template <int TH, bool FWD>
 __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, const DevInst &D,
                           int epoch, int kcur, bool &self_again, unsigned &nbmask) {
     constexpr int BR = BFS_ROWS;
@@ -882,12 +890,26 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     // k = 0..5 masks R, D, U, E, Q, V; 6..8 residuals up from row 0, down
     // into row 0, up into the last row; 9 + i the label of row i.
     int32_t *REC = P.strip_cache + (size_t)(D.lead_base + (T.ty / SPAN) * D.tiles_x + T.tx) * STRIP_REC_WORDS;
+    // the forward pass keeps its labels in the records only (the distances to
+    // t in the label plane stay for push/relabel), so it reads neighbouring
+    // strips' labels there: the left strip's column 30, the right strip's
+    // column 1, the last row of the strip above, the first row of the one below
+    const int32_t *REC_L = REC - STRIP_REC_WORDS, *REC_R = REC + STRIP_REC_WORDS;
+    const int32_t *REC_T = REC - (size_t)D.tiles_x * STRIP_REC_WORDS;
+    const int32_t *REC_B = REC + (size_t)D.tiles_x * STRIP_REC_WORDS;
+    auto ghost_label = [&](int i) -> int {      // lanes 0 and 31, row i, neighbour visited
+        if constexpr (FWD) return __ldcg(lane == 0 ? REC_L + (9 + i) * 32 + 30 : REC_R + (9 + i) * 32 + 1);
+        else return __ldcg(Hh + (size_t)(T.y0 + i) * pitch + T.X);
+    };
     int(*Dl)[33] = S.d;
     unsigned bR = 0, bD = 0, bU = 0, bE = 0, bQ = 0, bV = 0;
     int hT = HINF, res_up0 = 0, res_down_above = 0, res_up_last = 0, dold_top = HINF, dold_bot = HINF;
     const bool below = T.y0 + BR < D.rows;
     int hB = HINF;
-    if (own && vB && below) hB = __ldcg(Hh + (size_t)(T.y0 + BR) * pitch + T.X);
+    if (own && vB && below) {
+        if constexpr (FWD) hB = __ldcg(REC_B + 9 * 32 + lane);
+        else hB = __ldcg(Hh + (size_t)(T.y0 + BR) * pitch + T.X);
+    }
     if (own_valid) {
         // a second visit in this epoch: masks and residuals from the record,
         // labels of this strip's own columns from the record, the ghost
@@ -901,7 +923,10 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
         res_up0 = __ldcg(REC + 6 * 32 + lane);
         res_down_above = __ldcg(REC + 7 * 32 + lane);
         res_up_last = __ldcg(REC + 8 * 32 + lane);
-        if (own && T.y0 > 0 && vT) hT = __ldcg(Hh + (size_t)(T.y0 - 1) * pitch + T.X);
+        if (own && T.y0 > 0 && vT) {
+            if constexpr (FWD) hT = __ldcg(REC_T + (9 + BR - 1) * 32 + lane);
+            else hT = __ldcg(Hh + (size_t)(T.y0 - 1) * pitch + T.X);
+        }
         constexpr int LH = 16;
 #pragma unroll 1
         for (int c0 = 0; c0 < BR; c0 += LH) {
@@ -910,8 +935,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
             for (int j = 0; j < LH; ++j) {
                 const int i = c0 + j;
                 const bool rowok = T.y0 + i < D.rows;
-                dv[j] = own ? __ldcg(REC + (9 + i) * 32 + lane)
-                            : (T.inb && rowok && vX) ? __ldcg(Hh + (size_t)(T.y0 + i) * pitch + T.X) : HINF;
+                dv[j] = own ? __ldcg(REC + (9 + i) * 32 + lane) : (T.inb && rowok && vX) ? ghost_label(i) : HINF;
             }
 #pragma unroll
             for (int j = 0; j < LH; ++j) {
@@ -930,7 +954,10 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
         const int wvT = __ldg(WV + j), fdT = __ldcg(FD + j);
         res_up0 = wvT + fdT;          // row 0 -> above
         res_down_above = wvT - fdT;   // above -> row 0
-        if (vT) hT = __ldcg(Hh + j);
+        if (vT) {
+            if constexpr (FWD) hT = __ldcg(REC_T + (9 + BR - 1) * 32 + lane);
+            else hT = __ldcg(Hh + j);
+        }
     }
 
     // residual arcs as bit masks (bit i = row i): R/L/D/U = from the pixel to
@@ -959,7 +986,8 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
             wv[j] = ldo ? __ldg(WV + idx) : 0;
             rt[j] = ldo ? __ldcg(RT + idx) : 0;
             ev[j] = ldo ? __ldcg(E + idx) : 0;
-            dv[j] = (T.inb && rowok && vX) ? __ldcg(Hh + idx) : HINF;
+            if constexpr (FWD) dv[j] = (T.inb && rowok && vX) ? ghost_label(c0 + j) : HINF;
+            else dv[j] = (T.inb && rowok && vX) ? __ldcg(Hh + idx) : HINF;
         }
 #pragma unroll
         for (int j = 0; j < LB; ++j) {
@@ -978,7 +1006,10 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
             if (i == BR - 1) res_up_last = wv[j] + fd[j];     // below -> last row
             if (i == 0) dold_top = dv[j];
             if (i == BR - 1) dold_bot = dv[j];
-            Dl[i][lane] = (ldo && rt[j] > 0) ? min(dv[j], 1) : dv[j];
+            // distances to t start at 1 where the arc to t is residual; the
+            // forward pass starts at 0 on pixels holding excess
+            if constexpr (FWD) Dl[i][lane] = (ldo && ev[j] > 0) ? 0 : dv[j];
+            else Dl[i][lane] = (ldo && rt[j] > 0) ? min(dv[j], 1) : dv[j];
             if (lane == 1) S.dl0[0][i] = dv[j];
             if (lane == 30) S.dl0[1][i] = dv[j];
         }
@@ -998,6 +1029,18 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     // residual w + f towards it (bV of the lane on the left)
     unsigned bL = __shfl_up_sync(FULL_MASK, bV, 1);
     if (!own) bL = 0;
+    // arcs the relaxation follows, as masks: for distances to t the arcs out
+    // of the pixel (d(p) <= d(q) + 1 for p -> q); for the forward pass the arcs
+    // into it (d(p) <= d(q) + 1 for q -> p): from above (row i-1 down to i), from
+    // below (i+1 up to i), from the left column and from the right column
+    unsigned aU = bU, aD = bD, aL = bL, aR = bR;
+    if constexpr (FWD) {
+        aU = (bD << 1) | (res_down_above > 0 ? 1u : 0u);
+        aD = (bU >> 1) | (res_up_last > 0 ? 0x80000000u : 0u);
+        aL = __shfl_up_sync(FULL_MASK, bQ, 1);
+        aR = bV;
+        if (!own) aU = aD = aL = aR = 0;
+    }
 
     // d(p) <= d(q) + 1 for every residual arc p -> q, relaxed to the fixpoint
     // (ghost lanes only supply their neighbours' labels)
@@ -1006,8 +1049,8 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     unsigned rowR = 0, rowL = 0;
 #pragma unroll 4
     for (int i = 0; i < BR; ++i) {
-        const unsigned r = __ballot_sync(FULL_MASK, (bR >> i) & 1u);
-        const unsigned l = __ballot_sync(FULL_MASK, (bL >> i) & 1u);
+        const unsigned r = __ballot_sync(FULL_MASK, (aR >> i) & 1u);
+        const unsigned l = __ballot_sync(FULL_MASK, (aL >> i) & 1u);
         if (lane == i) { rowR = r; rowL = l; }
     }
     const long long c_loaded = P.trace ? clock64() + (Dl[0][lane] & 0) : 0;
@@ -1026,7 +1069,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
                 for (int j = 0; j < CH; ++j) d[j] = Dl[c0 + j][lane];
 #pragma unroll
                 for (int j = 0; j < CH; ++j) {
-                    const bool bb = ((bU >> (c0 + j)) & 1u) && up + 1 < d[j];
+                    const bool bb = ((aU >> (c0 + j)) & 1u) && up + 1 < d[j];
                     d[j] = bb ? up + 1 : d[j];
                     ch |= bb;
                     up = d[j];
@@ -1042,7 +1085,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
                 for (int j = 0; j < CH; ++j) d[j] = Dl[c0 + j][lane];
 #pragma unroll
                 for (int j = CH - 1; j >= 0; --j) {
-                    const bool bb = ((bD >> (c0 + j)) & 1u) && dn + 1 < d[j];
+                    const bool bb = ((aD >> (c0 + j)) & 1u) && dn + 1 < d[j];
                     d[j] = bb ? dn + 1 : d[j];
                     ch |= bb;
                     dn = d[j];
@@ -1082,14 +1125,17 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     // label is above d(p) + 1
     bool wT = false, wB = false, wL = false, wR = false;
     const int d_top = Dl[0][lane], d_bot = Dl[BR - 1][lane];
-    if (own && T.y0 > 0) wT = d_top < dold_top && res_down_above > 0 && d_top + 1 < hT;
+    // the arc across the border that the neighbour's label would follow
+    const bool arcT = FWD ? res_up0 > 0 : res_down_above > 0;
+    const bool arcB = FWD ? ((bD >> (BR - 1)) & 1u) != 0 : res_up_last > 0;
+    if (own && T.y0 > 0) wT = d_top < dold_top && arcT && d_top + 1 < hT;
     if (own && below && T.ty + SPAN < D.tiles_y)
-        wB = d_bot < dold_bot && res_up_last > 0 && d_bot + 1 < hB;
+        wB = d_bot < dold_bot && arcB && d_bot + 1 < hB;
     const unsigned qbits = __shfl_up_sync(FULL_MASK, bQ, 1);     // lane 0's arcs into lane 1
     // lanes 1 and 30 compare their column with the ghost column beside it
     if ((lane == 1 && own && T.tx > 0) || (lane == 30 && own && T.tx < D.tiles_x - 1)) {
         const int side = lane == 1 ? 0 : 1, q = lane == 1 ? 0 : 31;
-        const unsigned arcs = lane == 1 ? qbits : bV;
+        const unsigned arcs = FWD ? (lane == 1 ? bL : bR) : (lane == 1 ? qbits : bV);
         bool w = false;
 #pragma unroll 8
         for (int i = 0; i < BR; ++i) {
@@ -1115,7 +1161,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
         const size_t idx = (size_t)y * pitch + T.X;
         const int di = Dl[i][lane];
         if (own && y < D.rows) {
-            __stcg(Hh + idx, di);
+            if constexpr (!FWD) __stcg(Hh + idx, di);
             M[idx] = di >= HINF ? 1 : 0;
             dm = di < HINF ? max(dm, di) : dm;
         }
@@ -1131,9 +1177,10 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     dm = (int)__reduce_max_sync(FULL_MASK, (unsigned)dm);
     __threadfence();
     __syncwarp();
-    // member tile j's active count, lane j (the counts are warp-uniform)
+    // member tile j's active count, lane j (the counts are warp-uniform); the
+    // forward pass changes neither counts nor the largest distance
     int delta = 0;
-    if (lane < SPAN && T.ty + lane < D.tiles_y) {
+    if (!FWD && lane < SPAN && T.ty + lane < D.tiles_y) {
         int mine = 0;
 #pragma unroll
         for (int j = 0; j < SPAN; ++j) mine = (j == lane) ? cnt[j] : mine;
@@ -1147,7 +1194,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
 #pragma unroll
     for (int o = SPAN / 2; o > 0; o >>= 1) delta += __shfl_down_sync(FULL_MASK, delta, o);
     if (lane == 0) {
-        if (dm > 0) atomicMax(&P.ist[inst].dmax, dm);
+        if (!FWD && dm > 0) atomicMax(&P.ist[inst].dmax, dm);
         *(volatile int *)&TS->epoch = epoch;
         if (delta) atomicAdd(&P.ist[inst].active, delta);
         atomicAdd(&P.ist[inst].bfs_visits, 1ULL);
@@ -1216,11 +1263,14 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_ker
         unsigned nb = 0;
         // a relabel item must be a strip's leader tile: anything else means a
         // push/relabel item outlived its phase, which the phase changes rule out
-        const bool stray = phase == PH_BFS && ((g - D.tile_base) / D.tiles_x) % (BFS_ROWS / TH) != 0;
+        const bool strip = phase == PH_BFS || phase == PH_FWD;
+        const bool stray = strip && ((g - D.tile_base) / D.tiles_x) % (BFS_ROWS / TH) != 0;
         if (stray && lane == 0) atomicOr(&P.g->err, GE_PHASE);
         if (status == PMF_OK && phase == PH_PR) pr_visit<TH, PO>(P, S, g, inst, D, k, requeue, nb);
         else if (status == PMF_OK && phase == PH_BFS && !stray)
-            bfs_visit<TH>(P, S, g, inst, D, epoch, k, requeue, nb);
+            bfs_visit<TH, false>(P, S, g, inst, D, epoch, k, requeue, nb);
+        else if (status == PMF_OK && phase == PH_FWD && !stray)
+            bfs_visit<TH, true>(P, S, g, inst, D, epoch, k, requeue, nb);
         __threadfence();
         __syncwarp();
         if (prof) {

@@ -424,3 +424,45 @@ def test_grid_flow_value_rejects_violations():
          (np.abs(a[1][:-1]) <= np.asarray(im.w_v).reshape(H, W)[:-1]).all()
     if ok:
         assert oracle.grid_flow_value(*args, *a) == val
+
+
+# --------------------------------------------------------------------------
+# the s-t swap (Section 3.2): exchanging s and t (pairwise capacities are
+# symmetric) keeps the flow value, and the original maximal source set is the
+# complement of the swapped problem's minimal source set
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(8))
+def test_min_source_set_matches_brute_force(seed):
+    rng = np.random.default_rng(500 + seed)
+    n = 10
+    m = 30
+    tail = rng.integers(0, n, m)
+    head = rng.integers(0, n, m)
+    keep = tail != head
+    tail, head = tail[keep], head[keep]
+    cap = rng.integers(0, 6, len(tail))
+    val, fl, _ = oracle.maxflow(n, tail, head, cap, 0, n - 1)
+    reach = oracle.source_reach(n, tail, head, cap, fl, 0)
+    assert np.array_equal(reach, oracle.brute_force_min_source_set(n, tail, head, cap, 0, n - 1))
+
+
+@pytest.mark.parametrize("shape,seed", [((3, 4), 0), ((4, 4), 1), ((2, 7), 2), ((6, 9), 3), ((12, 15), 4)])
+def test_swap_keeps_value_and_complements_the_minimal_source_set(shape, seed):
+    H, W = shape
+    rng = np.random.default_rng(900 + seed)
+    wl = inputs.random_grid(H, W, rng, p_zero=0.3, n_lambda=3)
+    im, inst = wl.images[0], wl.instances[0]
+    N = H * W
+    for lam in inst.lambdas:
+        cs = (np.asarray(inst.src0, np.int64) + np.asarray(inst.slope, np.int64) * int(lam)).astype(np.int32)
+        f, m = oracle.grid_solve(H, W, im.w_h, im.w_v, inst.src0, inst.slope, inst.sink, [int(lam)])
+        # swapped: source capacities = the sink capacities, sink capacities = cs(lambda)
+        zero = np.zeros_like(cs)
+        tail, head, cap = oracle.grid_arcs(H, W, im.w_h, im.w_v, inst.sink, zero, cs, 0)
+        val, fl, _ = oracle.maxflow(N + 2, tail, head, cap, N, N + 1)
+        assert val == int(f[0])
+        minsrc = oracle.source_reach(N + 2, tail, head, cap, fl, N)[:N].reshape(H, W)
+        assert np.array_equal(1 - minsrc, m[0])
+        if N <= 16:
+            bf = oracle.brute_force_min_source_set(N + 2, tail, head, cap, N, N + 1)[:N].reshape(H, W)
+            assert np.array_equal(bf, minsrc)

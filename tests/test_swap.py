@@ -1,0 +1,93 @@
+"""The s-t swap (Section 3.2): the rule on the CPU, and on the GPU, solves of
+the exchanged problems whose flows and masks must equal the oracle's for the
+original problems (the mask comes back as the original maximal source set:
+the complement of the exchanged problem's minimal source set)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1509_06004_b300 import inputs, swap
+
+
+def test_sign_count_rule():
+    src0 = np.array([0, 0, 0, 0], np.int32)
+    slope = np.array([1, 1, 1, 1], np.int32)
+    sink = np.array([5, 5, 5, 1], np.int32)
+    assert swap.needs_swap(src0, slope, sink, 2)          # three of four below their sink capacity
+    assert not swap.needs_swap(src0, slope, sink, 5)      # no negative differences at all
+    assert not swap.needs_swap(src0, slope, sink, 6)
+    a, b, c = swap.swapped_terminals(src0, slope, sink, 3)
+    assert np.array_equal(a, sink) and not b.any() and np.array_equal(c, src0 + 3 * slope)
+
+
+def test_rule_counts_strictly():
+    # at lambda 5: differences (-5+5, ..) = (0, 0, 0, 4): no negatives -> no swap
+    src0 = np.zeros(4, np.int32)
+    slope = np.ones(4, np.int32)
+    sink = np.array([5, 5, 5, 1], np.int32)
+    d = src0 + slope * 5 - sink
+    assert (d < 0).sum() == 0 and not swap.needs_swap(src0, slope, sink, 5)
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_06004_b300 import build
+    build.build()
+    return True
+
+
+def _check(wl, mode):
+    st, res, sw = swap.solve_workload(wl, swap=mode)
+    ref = oracle.solve_workload(wl)
+    for i, ((f, m), (of, om)) in enumerate(zip(res, ref)):
+        assert all(s == 0 for s in st[i]), st[i]
+        assert np.array_equal(f, of), (i, f, of)
+        assert np.array_equal(m, om), (i, np.argwhere(m != om)[:5])
+    return sw
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", [(1, 1), (1, 9), (9, 1), (7, 33), (16, 31), (33, 97), (40, 70)])
+@pytest.mark.parametrize("mode", ["always", "auto"])
+def test_swapped_random_grids(gpu, shape, mode):
+    H, W = shape
+    rng = np.random.default_rng(31 * H + W)
+    wl = inputs.random_grid(H, W, rng, wmax=20, tmax=40, p_zero=0.2, n_lambda=4, lam_max=30)
+    sw = _check(wl, mode)
+    if mode == "always":
+        assert all(all(x) for x in sw)
+
+
+@pytest.mark.gpu
+def test_swapped_segmentation_schedule(gpu):
+    """A synthetic segmentation instance over its full lambda schedule: the
+    rule swaps the low lambdas (sink-dominated) and keeps the high ones."""
+    wl = inputs.parametric_320x240(n_lambda=8)
+    sw = _check(wl, "auto")
+    assert any(sw[0]) and not all(sw[0])
+
+
+@pytest.mark.gpu
+def test_cut_rule_on_a_multi_lambda_constant_problem(gpu):
+    """Rule 1 on a warm-started schedule of a lambda-independent problem: the
+    forward pass runs after every certified step and the next step starts
+    from the same labels; every step returns the same flow and cut."""
+    from paper_1509_06004_b300 import pmf
+    wl = inputs.random_grid(24, 40, np.random.default_rng(5), wmax=20, tmax=40, p_zero=0.2, n_lambda=1)
+    inst = wl.instances[0]
+    a, b, c = swap.swapped_terminals(inst.src0, inst.slope, inst.sink, int(inst.lambdas[0]))
+    sw = inputs.Workload("sw", wl.images, [inputs.Instance(0, a, b, c, np.array([3, 5, 9], np.int32))])
+    bt = pmf.batch_from_workload(sw)
+    bt.set_cut_rule(0, 1)
+    bt.solve(np.array([[3, 5, 9]], np.int32))
+    assert all(s == 0 for s in bt.sync(check=False))
+    f, m = oracle.grid_solve(24, 40, wl.images[0].w_h, wl.images[0].w_v, inst.src0, inst.slope, inst.sink,
+                             [int(inst.lambdas[0])])
+    flows, cuts = bt.flows(0), bt.cuts(0)
+    bt.close()
+    assert np.all(flows == f[0])
+    for k in range(3):
+        assert np.array_equal(cuts[k], m[0])
