@@ -398,14 +398,19 @@ def serving_bench(args, dev):
     the same stream one request at a time on the whole GPU."""
     import torch
     from paper_1509_06004_b300 import serving
-    reqs = inputs.serving_stream(args.serving_rate, args.serving_requests, seed=0, max_side=args.serving_max_side)
+    # the first serving_warmup requests of the stream are served but left out
+    # of the latency figures (the stream is already running when measurement starts)
+    nw = args.serving_warmup
+    reqs = inputs.serving_stream(args.serving_rate, nw + args.serving_requests, seed=0,
+                                 max_side=args.serving_max_side)
     warm = inputs.serving_stream(args.serving_rate, 3, seed=99, max_side=args.serving_max_side)
-    out = {"rate_per_s": args.serving_rate, "requests": len(reqs), "max_side": args.serving_max_side,
-           "budget_bytes": args.serving_budget, "pixel_solves": sum(r.workload.pixel_solves for r in reqs)}
+    out = {"rate_per_s": args.serving_rate, "requests": args.serving_requests, "warmup_requests": nw,
+           "max_side": args.serving_max_side, "budget_bytes": args.serving_budget,
+           "pixel_solves": sum(r.workload.pixel_solves for r in reqs[nw:])}
     for name, slots in (("continuous", args.serving_slots), ("one_at_a_time", 1)):
         serving.serve(warm, slots=slots, budget_bytes=args.serving_budget, device=dev.index)
         st = serving.serve(reqs, slots=slots, budget_bytes=args.serving_budget, device=dev.index)
-        out[name] = st.summary()
+        out[name] = st.summary(skip=nw)
         out[name]["slots"] = slots
         torch.cuda.empty_cache()
     return out
@@ -481,6 +486,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=40, help="0 = skip the serving run")
     ap.add_argument("--serving-rate", type=float, default=50.0)
+    ap.add_argument("--serving-warmup", type=int, default=0, help="leading requests left out of the latencies")
     ap.add_argument("--serving-max-side", type=int, default=800)
     ap.add_argument("--serving-slots", type=int, default=4)
     ap.add_argument("--serving-budget", type=int, default=64 << 30)

@@ -48,10 +48,13 @@ class ServeStats:
     peak_bytes: int = 0
     max_concurrent: int = 0
 
-    def summary(self) -> dict:
-        lat = np.array([c.latency_s for c in self.completed]) * 1e3
+    def summary(self, skip: int = 0) -> dict:
+        """Latency percentiles over the requests with index >= skip (the
+        first ones warm the stream up); throughput over the whole run."""
+        meas = [c for c in self.completed if c.index >= skip]
+        lat = np.array([c.latency_s for c in meas]) * 1e3
         pix = sum(c.pixel_solves for c in self.completed)
-        return {"requests": len(self.completed),
+        return {"requests": len(meas),
                 "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
                 "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
                 "mean_ms": float(lat.mean()) if len(lat) else None,

@@ -72,6 +72,19 @@ def test_scheduler_slots_budget_and_fifo():
     assert all(x.latency_s >= 0.1 - 1e-9 for x in st.completed)
 
 
+def test_summary_skips_warmup_requests():
+    """Latency figures cover only the requests after the warm-up ones; the
+    throughput covers the whole run."""
+    clk = Clock()
+    be = FakeBackend(clk, budget=100, dur=0.1)
+    reqs = [Req(0.0, 10) for _ in range(4)] + [Req(1.0, 10) for _ in range(4)]
+    st = serving.Scheduler(be, slots=4, budget_bytes=100).run(reqs, realtime=True, clock=clk, sleep=clk.sleep)
+    full, part = st.summary(), st.summary(skip=4)
+    assert full["requests"] == 8 and part["requests"] == 4
+    assert part["pixel_solves_per_s"] == full["pixel_solves_per_s"]
+    assert part["p50_ms"] <= full["p99_ms"]
+
+
 def test_scheduler_rejects_oversized_request():
     clk = Clock()
     with pytest.raises(ValueError):
