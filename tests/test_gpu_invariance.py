@@ -124,7 +124,7 @@ def test_supergraph_480x320_sampled_at_bench_configuration(P):
     from paper_1509_06004_b300 import autotune
     wl = inputs.supergraph_480x320()
     c = autotune.cached(wl) or {"segments": 5, **autotune.DEFAULTS}
-    knobs = {k: c[k] for k in autotune.DEFAULTS}
+    knobs = {k: c.get(k, v) for k, v in autotune.DEFAULTS.items()}
     run = wl.split_segments(c["segments"]) if c["segments"] > 1 else wl
     res = _solve(P, run, **knobs)
     rng = np.random.default_rng(0)
@@ -137,6 +137,25 @@ def test_supergraph_480x320_sampled_at_bench_configuration(P):
         assert res[i][0][k] == of[0]
         assert np.array_equal(res[i][1][k], om[0])
     # properties that hold at any size: nested cuts and nondecreasing flows along each piece
+    for f, m in res:
+        assert np.all(np.diff(f) >= 0)
+        assert np.all(m[:-1] <= m[1:])
+
+
+def test_large_image_sampled(P):
+    """A 770 x 1010 image (no side a multiple of the tile or strip sizes):
+    sampled flows and masks equal the oracle's; cuts nested, flows
+    nondecreasing along each schedule."""
+    wl = _synthetic(77, 770, 1010, 2, 3, lo=20, hi=400)
+    res = _solve(P, wl, push_order=1)
+    rng = np.random.default_rng(2)
+    for i, k in ((0, int(rng.integers(0, 3))), (1, int(rng.integers(0, 3)))):
+        inst = wl.instances[i]
+        im = wl.images[inst.image]
+        of, om = oracle.grid_solve(im.H, im.W, im.w_h, im.w_v, inst.src0, inst.slope, inst.sink,
+                                   [inst.lambdas[k]])
+        assert res[i][0][k] == of[0]
+        assert np.array_equal(res[i][1][k], om[0])
     for f, m in res:
         assert np.all(np.diff(f) >= 0)
         assert np.all(m[:-1] <= m[1:])
