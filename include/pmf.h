@@ -156,15 +156,21 @@ PMF_API pmf_status pmf_get_tuning(const pmf_batch *b, pmf_tuning *t);
 /* Pairwise capacities of one image (Section 2: the smoothness edges).
  * w_h[y*W + x] joins (y,x)-(y,x+1), w_v[y*W + x] joins (y,x)-(y+1,x); the last
  * column of w_h and the last row of w_v are ignored.  on_device = 1: device
- * pointers (checked on the device, errors reported by pmf_sync); 0: host
- * pointers (checked here, PMF_ERR_INVALID_ARG / PMF_ERR_OVERFLOW). */
+ * pointers (checked on the device, errors reported by pmf_sync; the arrays are
+ * read by work queued on the batch's stream); 0: host pointers, copied and
+ * checked on the device before the call returns (PMF_ERR_INVALID_ARG for a
+ * negative capacity, PMF_ERR_OVERFLOW above the maximum); the host arrays may
+ * be reused as soon as it returns.  After an error the image (or instance) is
+ * marked invalid until a later call succeeds: a solve in between reports the
+ * error for the instances concerned. */
 PMF_API pmf_status pmf_set_capacities(pmf_batch *b, int32_t image, const int32_t *w_h,
                               const int32_t *w_v, int on_device);
 
 /* Terminal capacities of one instance (Section 2: the unary edges; Section
  * 2.1: the lambda-dependent source side).  cs(p, lambda) = src0[p] +
- * slope[p]*lambda, ct(p) = sink[p].  slope < 0 gives PMF_ERR_NOT_MONOTONE.
- * on_device as for pmf_set_capacities. */
+ * slope[p]*lambda, ct(p) = sink[p].  slope < 0 gives PMF_ERR_NOT_MONOTONE
+ * (reported first), a capacity above PMF_INF PMF_ERR_OVERFLOW, a negative one
+ * PMF_ERR_INVALID_ARG.  on_device as for pmf_set_capacities. */
 PMF_API pmf_status pmf_set_terminals(pmf_batch *b, int32_t inst, const int32_t *src0,
                              const int32_t *slope, const int32_t *sink, int on_device);
 
