@@ -485,7 +485,7 @@ pmf_status pmf_set_capacities(pmf_batch *b, int32_t image, const int32_t *w_h, c
     cudaStream_t s = b->setup_stream;
     const int32_t *src_h = w_h, *src_v = w_v;
     if (!on_device) {
-        // checked on the device by the padding kernel, verdict read back below
+        // checked on the device by the padding kernel, the result read back below
         int32_t *stg = (int32_t *)(b->ws + b->L.staging);
         cudaError_t e = cudaMemcpyAsync(stg, w_h, n * 4, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(stg + n, w_v, n * 4, cudaMemcpyHostToDevice, s);
@@ -536,7 +536,7 @@ pmf_status pmf_set_terminals(pmf_batch *b, int32_t inst, const int32_t *src0, co
     const int32_t *a = src0, *c = slope, *k = sink;
     if (!on_device) {
         // host arrays are checked on the device by the padding kernel (a host
-        // loop is memory-bound at ~10 GB/s on one core) and the verdict is
+        // loop is memory-bound at ~10 GB/s on one core) and the result is
         // read back before returning
         int32_t *stg = (int32_t *)(b->ws + b->L.staging);
         cudaError_t e = cudaMemcpyAsync(stg, src0, n * 4, cudaMemcpyHostToDevice, s);
