@@ -128,6 +128,9 @@ typedef struct {
     int32_t epoch;           /* global relabel count */
     int64_t pr_visits;       /* cumulative push/relabel tile visits */
     int64_t bfs_visits;      /* cumulative relabel tile visits */
+    int64_t flow;            /* flow into t so far */
+    int32_t active;          /* pixels with excess that can reach t, as of the last relabel */
+    int32_t reserved;
 } pmf_trace_event;
 
 /* Per-instance counters of the last solve (pmf_get_stats). */

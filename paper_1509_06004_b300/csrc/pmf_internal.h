@@ -80,6 +80,8 @@ struct TraceEvent {
     unsigned long long t_ns;
     int32_t inst, event, k, epoch;
     long long pr_visits, bfs_visits;
+    long long flow;              // flow into t so far (current lambda step)
+    int32_t active, pad_;        // pixels with excess that reach t, as of the last relabel
 };
 enum TraceKind { TR_BFS_START = 0, TR_STEP_DONE = 1, TR_PR_START = 2, TR_DONE = 3, TR_NOT_CONVERGED = 4 };
 constexpr int TRACE_CAP = 1 << 16;

@@ -260,6 +260,9 @@ __device__ void trace(const Params &P, int inst, int event, volatile InstState *
     e.epoch = S->epoch;
     e.pr_visits = (long long)S->pr_visits;
     e.bfs_visits = (long long)S->bfs_visits;
+    e.flow = (long long)S->flow;
+    e.active = S->active;
+    e.pad_ = 0;
     P.trace[i] = e;
 }
 

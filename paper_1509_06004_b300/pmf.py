@@ -73,7 +73,8 @@ class Tuning(ctypes.Structure):
 class TraceEvent(ctypes.Structure):
     _fields_ = [("t_ns", ctypes.c_uint64), ("inst", ctypes.c_int32), ("event", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("epoch", ctypes.c_int32), ("pr_visits", ctypes.c_int64),
-                ("bfs_visits", ctypes.c_int64)]
+                ("bfs_visits", ctypes.c_int64), ("flow", ctypes.c_int64), ("active", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 TRACE_EVENTS = {0: "relabel", 1: "step-done", 2: "push-relabel", 3: "done", 4: "not-converged"}
