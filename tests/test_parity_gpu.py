@@ -70,3 +70,31 @@ def test_parametric_320x240(pmf):
     flows, masks = res[0]
     for k in range(len(flows) - 1):
         assert np.all(masks[k] <= masks[k + 1])
+
+
+@pytest.mark.parametrize("case", range(24))
+def test_fuzz_shapes_knobs_and_schedules(pmf, case):
+    """Seeded random instances: grid shape (1 to 90 a side), capacity ranges
+    and share of zero capacities, schedule length, batch size (1 to 4
+    instances on up to 2 images), and solver knobs (tile height, push order,
+    sweeps, relabel cadence, label slack, grid size).  Flows and masks must
+    equal the oracle's bit for bit."""
+    rng = np.random.default_rng(7000 + case)
+    wl = inputs.Workload(f"fuzz{case}")
+    n_img = int(rng.integers(1, 3))
+    for _ in range(n_img):
+        H, W = int(rng.integers(1, 91)), int(rng.integers(1, 91))
+        g = inputs.random_grid(H, W, rng, wmax=int(rng.choice([3, 20, 1000])), tmax=int(rng.choice([5, 40, 2000])),
+                               p_zero=float(rng.uniform(0, 0.5)), n_lambda=1)
+        wl.images.append(g.images[0])
+    m = int(rng.integers(1, 6))
+    for _ in range(int(rng.integers(1, 5))):
+        i = int(rng.integers(0, n_img))
+        g = inputs.random_grid(wl.images[i].H, wl.images[i].W, rng, wmax=1, tmax=int(rng.choice([5, 40, 2000])),
+                               p_zero=float(rng.uniform(0, 0.5)), n_lambda=m, lam_max=int(rng.choice([5, 50, 3000])))
+        inst = g.instances[0]
+        wl.instances.append(inputs.Instance(i, inst.src0, inst.slope, inst.sink, inst.lambdas))
+    knobs = dict(tile_h=int(rng.choice([4, 8])), push_order=int(rng.integers(0, 2)),
+                 sweeps=int(rng.choice([1, 2, 4, 8, 16])), relabel_every=int(rng.choice([50, 200, 800, 3200])),
+                 label_slack=int(rng.choice([-1, 1, 4, 16])), grid_blocks=int(rng.choice([0, 1, 7, 64])))
+    check_workload(pmf, wl, **knobs)
