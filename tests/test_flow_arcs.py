@@ -101,3 +101,38 @@ def test_not_ready_before_a_solve(P):
         b.flow_arcs(0)
     assert ei.value.status == P.PMF_ERR_NOT_READY
     b.close()
+
+
+def test_large_grid_properties(P):
+    """A 4099 x 4100 grid (16.8 M pixels; sides that are no multiple of the
+    tile, strip or pitch sizes), two lambdas: the per-arc flow is feasible by
+    the oracle's conditions with the value the solver reports, its cut is
+    saturated, and the two cuts are nested.  (The oracle's max-flow would take
+    too long here; these properties hold at any size.)"""
+    H, W = 4099, 4100
+    rng = np.random.default_rng(17)
+    img = inputs.make_image(H, W, 5, 0.05, rng)
+    w_h, w_v = inputs.pairwise_caps(img)
+    y0, x0 = inputs.random_seed_origin(H, W, rng)
+    src0, slope, sink = inputs.terminals(img, inputs.seed_square(H, W, y0, x0))
+    wl = inputs.Workload("large", [inputs.Image(H, W, w_h, w_v, None)],
+                         [inputs.Instance(0, src0, slope, sink, np.array([40, 300], np.int32))])
+    b = P.batch_from_workload(wl, push_order=1)
+    b.solve(np.array([[40, 300]], np.int32))
+    assert all(s == P.PMF_OK for s in b.sync(check=False))
+    flows, cuts = b.flows(0), b.cuts(0)
+    assert np.all(cuts[0] <= cuts[1]) and flows[0] <= flows[1]
+    arcs = b.flow_arcs(0)
+    val = oracle.grid_flow_value(H, W, w_h, w_v, src0, slope, sink, 300,
+                                 arcs["f_h"], arcs["f_v"], arcs["f_s"], arcs["f_t"])
+    assert val == int(flows[1])
+    # the flow saturates the reported cut: every pair arc from the source set
+    # to the rest carries its capacity outwards, so the cut's capacity is the value
+    m = cuts[1].astype(bool)
+    fh, fv = arcs["f_h"].astype(np.int64), arcs["f_v"].astype(np.int64)
+    wh, wv = np.asarray(w_h, np.int64), np.asarray(w_v, np.int64)
+    a, c = m[:, :-1], m[:, 1:]
+    assert np.all(fh[:, :-1][a & ~c] == wh[:, :-1][a & ~c]) and np.all(fh[:, :-1][~a & c] == -wh[:, :-1][~a & c])
+    a, c = m[:-1], m[1:]
+    assert np.all(fv[:-1][a & ~c] == wv[:-1][a & ~c]) and np.all(fv[:-1][~a & c] == -wv[:-1][~a & c])
+    b.close()
