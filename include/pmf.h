@@ -216,8 +216,8 @@ PMF_API pmf_status pmf_get_cut(pmf_batch *b, int32_t inst, int32_t k, uint8_t *m
  * cost), after pmf_sync. */
 PMF_API pmf_status pmf_get_flow(pmf_batch *b, int32_t inst, int32_t k, int64_t *flow);
 
-/* Every mask of instance inst: n_lambda * H * W bytes, [k][y][x], one copy per
- * lambda and a single synchronisation (on_device as for pmf_get_cut). */
+/* Every mask of instance inst: n_lambda * H * W bytes, [k][y][x], as one copy
+ * and a single synchronisation (on_device as for pmf_get_cut). */
 PMF_API pmf_status pmf_get_cuts(pmf_batch *b, int32_t inst, uint8_t *masks, int on_device);
 
 /* Every flow value of instance inst: n_lambda int64 (host pointer). */

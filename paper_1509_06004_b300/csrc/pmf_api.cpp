@@ -708,13 +708,13 @@ pmf_status pmf_get_cuts(pmf_batch *b, int32_t inst, uint8_t *masks, int on_devic
     if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->last_n_lambda) return PMF_ERR_NOT_READY;
     DeviceGuard dg(b->device);
     const DevInst &d = b->dinst[inst];
-    const size_t ps = (size_t)d.rows * d.pitch, hw = (size_t)d.H * d.W;
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < b->last_n_lambda && e == cudaSuccess; ++k) {
-        const char *src = b->ws + b->L.masks + d.mask_off + (size_t)k * ps;
-        e = cudaMemcpy2DAsync(masks + (size_t)k * hw, d.W, src, d.pitch, d.W, d.H,
-                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->cap_stream);
-    }
+    // all lambdas in one 3-D copy: source slices rows x pitch, destination H x W
+    cudaMemcpy3DParms p = {};
+    p.srcPtr = make_cudaPitchedPtr(b->ws + b->L.masks + d.mask_off, (size_t)d.pitch, (size_t)d.W, (size_t)d.rows);
+    p.dstPtr = make_cudaPitchedPtr(masks, (size_t)d.W, (size_t)d.W, (size_t)d.H);
+    p.extent = make_cudaExtent((size_t)d.W, (size_t)d.H, (size_t)b->last_n_lambda);
+    p.kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpy3DAsync(&p, b->cap_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap_stream);
     return cuda_err(e);
 }

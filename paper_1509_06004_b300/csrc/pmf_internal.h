@@ -52,20 +52,20 @@ struct DevInst {                 // read-only during a solve
 
 // 16-byte aligned: the worker reads the first four fields with one 16-byte
 // vector load, which faults on a misaligned address
-struct alignas(16) InstState {   // mutable during a solve
+struct alignas(128) InstState {  // mutable during a solve
     // written only by the warp that runs a phase change (nothing of the
     // instance is queued or running then); read by the workers
     int32_t phase, k, epoch, status;
     int32_t vflags;                  // validation flags of the inputs
     int32_t pr_budget;               // push/relabel visits allowed before the next global relabel
-    int32_t dmax;                    // largest finite distance found by the current relabel
+    int32_t want_bfs;                // set once by the visit that spends the budget
     int32_t lab_cap;                 // labels at or above this are treated as "cannot reach t"
     unsigned long long pr_mark;      // pr_visits when the current push/relabel phase began
     unsigned long long step_mark;    // pr_visits + bfs_visits when the current lambda step began
     unsigned long long epochs;       // global relabels so far
     int32_t pad_b_, pad_c_;
-    // updated atomically by the workers
-    int32_t outstanding, active, want_bfs, pad3_;
+    // updated atomically by the workers, on their own cache line
+    alignas(128) int32_t outstanding, active, dmax, pad3_;
     unsigned long long flow;         // int64 two's complement: total flow into t
     unsigned long long pr_visits, bfs_visits;
 };
