@@ -296,16 +296,24 @@ def run_ours(args, rank, world, dev):
     return out
 
 
+def kernel_source_hash() -> str:
+    """sha256[:16] of the worker's sources: the kernel file and the header that
+    fixes its data layout (a profile is only quoted for the build it measured)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("pmf_kernels.cu", "pmf_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1509_06004_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _profiled_traffic(args, wl):
     """DRAM bytes per worker launch from the committed ncu summary
     (profiles/worker_kernel_traffic.txt) when it was taken on the current
     kernel source and matches this workload and mode; None otherwise."""
-    import hashlib
     p = os.path.join(ROOT, "profiles", "worker_kernel_traffic.txt")
-    src = os.path.join(ROOT, "paper_1509_06004_b300", "csrc", "pmf_kernels.cu")
     try:
         lines = [l.strip() for l in open(p) if l.strip() and not l.startswith("#")]
-        cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        cur = kernel_source_hash()
     except OSError:
         return None
     kv = dict(l.rsplit(":", 1) for l in lines)
