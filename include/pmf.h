@@ -202,6 +202,18 @@ PMF_API pmf_status pmf_set_cut_rule(pmf_batch *b, int32_t inst, int32_t rule);
 PMF_API pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_lambda,
                               void *cuda_stream);
 
+/* As pmf_solve_schedule, with a schedule length per instance (one launch for
+ * instances whose lambda counts differ, Section 3.1's supergraph of uneven
+ * parametric problems).  lambdas is a host array [n_inst][stride]; instance i
+ * solves its first lengths[i] values, which must be nondecreasing
+ * (1 <= lengths[i] <= stride <= max_lambdas; entries past lengths[i] are
+ * ignored).  lengths is a host array of n_inst values.  Results of instance i
+ * are indexed k < lengths[i] (pmf_get_cut / pmf_get_flow), and
+ * pmf_get_cuts / pmf_get_flows return lengths[i] entries.  Errors as
+ * pmf_solve_schedule; NULL lengths is PMF_ERR_INVALID_ARG. */
+PMF_API pmf_status pmf_solve_schedules(pmf_batch *b, const int32_t *lambdas, const int32_t *lengths,
+                                       int32_t stride, void *cuda_stream);
+
 /* Wait for the last solve.  per_instance (host, may be NULL) receives each
  * instance's pmf_status.  Returns PMF_OK iff every instance converged. */
 PMF_API pmf_status pmf_sync(pmf_batch *b, pmf_status *per_instance);
@@ -217,10 +229,12 @@ PMF_API pmf_status pmf_get_cut(pmf_batch *b, int32_t inst, int32_t k, uint8_t *m
 PMF_API pmf_status pmf_get_flow(pmf_batch *b, int32_t inst, int32_t k, int64_t *flow);
 
 /* Every mask of instance inst: n_lambda * H * W bytes, [k][y][x], as one copy
- * and a single synchronisation (on_device as for pmf_get_cut). */
+ * and a single synchronisation (on_device as for pmf_get_cut); n_lambda is the
+ * instance's schedule length in the last solve. */
 PMF_API pmf_status pmf_get_cuts(pmf_batch *b, int32_t inst, uint8_t *masks, int on_device);
 
-/* Every flow value of instance inst: n_lambda int64 (host pointer). */
+/* Every flow value of instance inst: its schedule length's worth of int64
+ * (host pointer). */
 PMF_API pmf_status pmf_get_flows(pmf_batch *b, int32_t inst, int64_t *flows);
 
 /* Device time of the last solve, from CUDA events the library records on the

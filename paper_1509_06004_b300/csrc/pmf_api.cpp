@@ -199,7 +199,7 @@ struct pmf_batch {
     float worker_ms_rounds = 0.f;
     bool in_flight = false;
     bool solved = false;
-    int32_t last_n_lambda = 0;
+    std::vector<int32_t> n_lam;            // schedule length of each instance in the last solve
     std::vector<DevInst> dinst;            // host copy of the descriptors
     // pinned host mirrors
     int32_t *lam_h = nullptr;
@@ -294,7 +294,7 @@ int grid_size(pmf_batch *b) {
 }
 
 // the launch sequence of one solve (persistent mode)
-pmf_status enqueue_solve(pmf_batch *b, int n_lambda, cudaStream_t s, bool capturing) {
+pmf_status enqueue_solve(pmf_batch *b, cudaStream_t s, bool capturing) {
     // inside a stream capture the timing events become event-record nodes
     auto rec = [&](cudaEvent_t ev) {
         return capturing ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal) : cudaEventRecord(ev, s);
@@ -317,7 +317,6 @@ pmf_status enqueue_solve(pmf_batch *b, int n_lambda, cudaStream_t s, bool captur
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->glob_h, b->ws + b->L.globals, sizeof(Globals), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = rec(b->ev_t1);
-    (void)n_lambda;
     return cuda_err(e);
 }
 
@@ -372,6 +371,7 @@ pmf_status pmf_create_batch(const pmf_batch_desc *desc, void *dev_workspace, siz
     b->device = desc->device;
     b->setup_stream = (cudaStream_t)cuda_stream;
     b->dinst.resize(desc->n_inst);
+    b->n_lam.assign(desc->n_inst, 0);
     apply_defaults(&b->tune);
     cudaError_t e = cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
     const size_t nl = (size_t)desc->n_inst * desc->max_lambdas;
@@ -560,19 +560,27 @@ pmf_status pmf_set_terminals(pmf_batch *b, int32_t inst, const int32_t *src0, co
     return host_flags_status(flags);
 }
 
-pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_lambda, void *cuda_stream) {
-    if (!b || !lambdas || n_lambda < 1 || n_lambda > b->desc.max_lambdas) return PMF_ERR_INVALID_ARG;
+// Both entry points: instance i solves lambdas[i * stride + 0 .. len(i) - 1],
+// len(i) = lengths ? lengths[i] : stride.
+static pmf_status solve_impl(pmf_batch *b, const int32_t *lambdas, const int32_t *lengths, int32_t stride,
+                             void *cuda_stream) {
+    if (!b || !lambdas || stride < 1 || stride > b->desc.max_lambdas) return PMF_ERR_INVALID_ARG;
+    auto len = [&](int i) { return lengths ? lengths[i] : stride; };
     for (int i = 0; i < b->desc.n_inst; ++i)
-        for (int k = 1; k < n_lambda; ++k)
-            if (lambdas[(size_t)i * n_lambda + k] < lambdas[(size_t)i * n_lambda + k - 1]) return PMF_ERR_NOT_MONOTONE;
+        if (len(i) < 1 || len(i) > stride) return PMF_ERR_INVALID_ARG;
+    for (int i = 0; i < b->desc.n_inst; ++i)
+        for (int k = 1; k < len(i); ++k)
+            if (lambdas[(size_t)i * stride + k] < lambdas[(size_t)i * stride + k - 1]) return PMF_ERR_NOT_MONOTONE;
     DeviceGuard dg(b->device);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (b->in_flight) { cudaEventSynchronize(b->done); b->in_flight = false; }
-    // lambda table [n_inst][max_lambdas] in pinned staging
+    // lambda table [n_inst][max_lambdas] in pinned staging (the last value
+    // repeated past an instance's length)
     for (int i = 0; i < b->desc.n_inst; ++i)
         for (int k = 0; k < b->desc.max_lambdas; ++k)
-            b->lam_h[(size_t)i * b->desc.max_lambdas + k] =
-                lambdas[(size_t)i * n_lambda + std::min(k, n_lambda - 1)];
+            b->lam_h[(size_t)i * b->desc.max_lambdas + k] = lambdas[(size_t)i * stride + std::min(k, len(i) - 1)];
+    bool len_changed = false;
+    for (int i = 0; i < b->desc.n_inst; ++i) len_changed |= b->n_lam[i] != len(i);
     b->P.trace = b->tune.trace ? (TraceEvent *)(b->ws + b->L.trace) : nullptr;
     b->P.sweeps = b->tune.sweeps;
     b->P.poll_ns = b->tune.poll_ns;
@@ -580,13 +588,12 @@ pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_la
     b->P.chain_push = b->tune.push_order;
     b->P.relabel_pct = b->tune.relabel_every;
     b->P.max_visits_per_tile = b->tune.max_visits_per_tile;
-    const bool geo_changed = (b->P.tile_h != b->tune.tile_h) || (b->last_n_lambda != n_lambda);
+    const bool geo_changed = (b->P.tile_h != b->tune.tile_h) || len_changed;
     if (geo_changed) {
-        // tile geometry and schedule length live in the descriptor table
-        for (int i = 0; i < b->desc.n_inst; ++i) b->dinst[i].n_lambda = n_lambda;
+        // tile geometry and schedule lengths live in the descriptor table
+        for (int i = 0; i < b->desc.n_inst; ++i) b->dinst[i].n_lambda = b->n_lam[i] = len(i);
         const pmf_status st = refresh_geometry(b, s);
         if (st != PMF_OK) return st;
-        b->last_n_lambda = n_lambda;
         b->graph_valid = false;
     }
     b->worker_grid = grid_size(b);
@@ -633,7 +640,7 @@ pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_la
             cudaGraph_t graph = nullptr;
             e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                const pmf_status st = enqueue_solve(b, n_lambda, b->cap_stream, true);
+                const pmf_status st = enqueue_solve(b, b->cap_stream, true);
                 const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
                 e = (st != PMF_OK) ? cudaErrorUnknown : e2;
             }
@@ -644,13 +651,23 @@ pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_la
         }
         e = cudaGraphLaunch(b->gexec, s);
     } else {
-        const pmf_status st = enqueue_solve(b, n_lambda, s, false);
+        const pmf_status st = enqueue_solve(b, s, false);
         if (st != PMF_OK) return st;
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->done, s);
     if (e != cudaSuccess) return cuda_err_at(e, "solve launch");
     b->in_flight = true;
     return PMF_OK;
+}
+
+pmf_status pmf_solve_schedule(pmf_batch *b, const int32_t *lambdas, int32_t n_lambda, void *cuda_stream) {
+    return solve_impl(b, lambdas, nullptr, n_lambda, cuda_stream);
+}
+
+pmf_status pmf_solve_schedules(pmf_batch *b, const int32_t *lambdas, const int32_t *lengths, int32_t stride,
+                               void *cuda_stream) {
+    if (!lengths) return PMF_ERR_INVALID_ARG;
+    return solve_impl(b, lambdas, lengths, stride, cuda_stream);
 }
 
 pmf_status pmf_sync(pmf_batch *b, pmf_status *per_instance) {
@@ -669,7 +686,7 @@ pmf_status pmf_sync(pmf_batch *b, pmf_status *per_instance) {
     for (int i = 0; i < b->desc.n_inst; ++i) {
         pmf_status st = (pmf_status)b->ist_h[i].status;
         if (internal && st == PMF_OK) st = PMF_ERR_NOT_CONVERGED;
-        if (st == PMF_OK && (b->ist_h[i].phase != PH_DONE || b->ist_h[i].k < b->last_n_lambda))
+        if (st == PMF_OK && (b->ist_h[i].phase != PH_DONE || b->ist_h[i].k < b->n_lam[i]))
             st = PMF_ERR_NOT_CONVERGED;
         if (gerr && st == PMF_OK && b->ist_h[i].phase != PH_DONE) st = PMF_ERR_NOT_CONVERGED;
         if (per_instance) per_instance[i] = st;
@@ -681,7 +698,7 @@ pmf_status pmf_sync(pmf_batch *b, pmf_status *per_instance) {
 pmf_status pmf_get_cut(pmf_batch *b, int32_t inst, int32_t k, uint8_t *mask, int on_device) {
     if (!b || !mask || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
     if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
-    if (k < 0 || k >= b->last_n_lambda) return PMF_ERR_INVALID_ARG;
+    if (k < 0 || k >= b->n_lam[inst]) return PMF_ERR_INVALID_ARG;
     if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k <= k) return PMF_ERR_NOT_READY;
     DeviceGuard dg(b->device);
     const DevInst &d = b->dinst[inst];
@@ -696,7 +713,7 @@ pmf_status pmf_get_cut(pmf_batch *b, int32_t inst, int32_t k, uint8_t *mask, int
 pmf_status pmf_get_flow(pmf_batch *b, int32_t inst, int32_t k, int64_t *flow) {
     if (!b || !flow || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
     if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
-    if (k < 0 || k >= b->last_n_lambda) return PMF_ERR_INVALID_ARG;
+    if (k < 0 || k >= b->n_lam[inst]) return PMF_ERR_INVALID_ARG;
     if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k <= k) return PMF_ERR_NOT_READY;
     *flow = b->flows_h[(size_t)inst * b->desc.max_lambdas + k];
     return PMF_OK;
@@ -705,14 +722,14 @@ pmf_status pmf_get_flow(pmf_batch *b, int32_t inst, int32_t k, int64_t *flow) {
 pmf_status pmf_get_cuts(pmf_batch *b, int32_t inst, uint8_t *masks, int on_device) {
     if (!b || !masks || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
     if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
-    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->last_n_lambda) return PMF_ERR_NOT_READY;
+    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->n_lam[inst]) return PMF_ERR_NOT_READY;
     DeviceGuard dg(b->device);
     const DevInst &d = b->dinst[inst];
     // all lambdas in one 3-D copy: source slices rows x pitch, destination H x W
     cudaMemcpy3DParms p = {};
     p.srcPtr = make_cudaPitchedPtr(b->ws + b->L.masks + d.mask_off, (size_t)d.pitch, (size_t)d.W, (size_t)d.rows);
     p.dstPtr = make_cudaPitchedPtr(masks, (size_t)d.W, (size_t)d.W, (size_t)d.H);
-    p.extent = make_cudaExtent((size_t)d.W, (size_t)d.H, (size_t)b->last_n_lambda);
+    p.extent = make_cudaExtent((size_t)d.W, (size_t)d.H, (size_t)b->n_lam[inst]);
     p.kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     cudaError_t e = cudaMemcpy3DAsync(&p, b->cap_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap_stream);
@@ -722,8 +739,8 @@ pmf_status pmf_get_cuts(pmf_batch *b, int32_t inst, uint8_t *masks, int on_devic
 pmf_status pmf_get_flows(pmf_batch *b, int32_t inst, int64_t *flows) {
     if (!b || !flows || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
     if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
-    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->last_n_lambda) return PMF_ERR_NOT_READY;
-    for (int k = 0; k < b->last_n_lambda; ++k) flows[k] = b->flows_h[(size_t)inst * b->desc.max_lambdas + k];
+    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->n_lam[inst]) return PMF_ERR_NOT_READY;
+    for (int k = 0; k < b->n_lam[inst]; ++k) flows[k] = b->flows_h[(size_t)inst * b->desc.max_lambdas + k];
     return PMF_OK;
 }
 
@@ -731,10 +748,10 @@ pmf_status pmf_get_flow_arcs(pmf_batch *b, int32_t inst, int32_t *f_h, int32_t *
                              int32_t *f_t) {
     if (!b || !f_h || !f_v || !f_s || !f_t || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
     if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
-    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->last_n_lambda) return PMF_ERR_NOT_READY;
+    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->n_lam[inst]) return PMF_ERR_NOT_READY;
     DeviceGuard dg(b->device);
     const DevInst &d = b->dinst[inst];
-    const int lambda = b->lam_h[(size_t)inst * b->desc.max_lambdas + b->last_n_lambda - 1];
+    const int lambda = b->lam_h[(size_t)inst * b->desc.max_lambdas + b->n_lam[inst] - 1];
     int32_t *status_d = (int32_t *)(b->ws + b->L.scratch);
     cudaStream_t s = b->cap_stream;
     cudaError_t e = launch_return_excess(b->P, d, lambda, 1 << 17, f_h, f_v, f_s, f_t, status_d, s);

@@ -187,6 +187,23 @@ class Workload:
                                               part.astype(np.int32), inst.seed_origin))
         return out
 
+    def split_pieces(self, lengths) -> "Workload":
+        """Every instance's schedule cut into consecutive pieces of the given
+        lengths (summing to the schedule length), each its own instance,
+        warm-started inside a piece and cold at its first lambda.  Unlike
+        split_segments the pieces may differ in length."""
+        lengths = [int(x) for x in lengths]
+        if min(lengths) < 1:
+            raise ValueError("pieces need at least one lambda")
+        out = Workload(self.name + "/pieces" + "-".join(map(str, lengths)), list(self.images), [])
+        for inst in self.instances:
+            if sum(lengths) != len(inst.lambdas):
+                raise ValueError(f"pieces {lengths} do not cover a schedule of {len(inst.lambdas)}")
+            for part in np.split(inst.lambdas, np.cumsum(lengths)[:-1]):
+                out.instances.append(Instance(inst.image, inst.src0, inst.slope, inst.sink,
+                                              part.astype(np.int32), inst.seed_origin))
+        return out
+
     def split_lambdas(self) -> "Workload":
         """The same solves with every (instance, lambda) as its own one-lambda
         instance (the lambda-concurrent form: no warm start between lambdas)."""

@@ -35,7 +35,7 @@ PMF_MAX_PAIRWISE = (1 << 28) - 1
 
 # every entry point declared in include/pmf.h
 EXPORTS = ["pmf_workspace_size", "pmf_create_batch", "pmf_set_tuning", "pmf_get_tuning",
-           "pmf_set_capacities", "pmf_set_terminals", "pmf_solve_schedule", "pmf_sync",
+           "pmf_set_capacities", "pmf_set_terminals", "pmf_solve_schedule", "pmf_solve_schedules", "pmf_sync",
            "pmf_get_cut", "pmf_get_flow", "pmf_get_cuts", "pmf_get_flows", "pmf_get_timing",
            "pmf_get_stats", "pmf_get_trace", "pmf_get_profile", "pmf_get_mask_layout",
            "pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error",
@@ -111,6 +111,7 @@ def lib(path: str | None = None):
             L.pmf_set_capacities.argtypes = [vp, i32, vp, vp, ctypes.c_int]
             L.pmf_set_terminals.argtypes = [vp, i32, vp, vp, vp, ctypes.c_int]
             L.pmf_solve_schedule.argtypes = [vp, i32p, i32, vp]
+            L.pmf_solve_schedules.argtypes = [vp, i32p, i32p, i32, vp]
             L.pmf_sync.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
             L.pmf_get_cut.argtypes = [vp, i32, i32, vp, ctypes.c_int]
             L.pmf_get_flow.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_int64)]
@@ -201,6 +202,7 @@ class Batch:
                "pmf_create_batch")
         self._h = h
         self.n_lambda = 0
+        self.lengths = [0] * len(self.inst_image)
 
     # -- set-up ------------------------------------------------------------------
     @staticmethod
@@ -252,13 +254,34 @@ class Batch:
 
     # -- solve -------------------------------------------------------------------
     def solve(self, lambdas, stream=None):
+        """lambdas: one schedule for every instance (1-D), a [n_inst][m] array,
+        or a list of per-instance 1-D schedules of different lengths
+        (pmf_solve_schedules)."""
+        strm = _stream_ptr(stream if stream is not None else self.stream)
+        if isinstance(lambdas, (list, tuple)) and len({len(np.ravel(x)) for x in lambdas}) > 1:
+            rows = [np.ascontiguousarray(np.ravel(x), np.int32) for x in lambdas]
+            if len(rows) != len(self.inst_image):
+                raise ValueError("one schedule per instance")
+            stride = max(len(r) for r in rows)
+            lam = np.zeros((len(rows), stride), np.int32)
+            for i, r in enumerate(rows):
+                lam[i, :len(r)] = r
+            lengths = np.array([len(r) for r in rows], np.int32)
+            self.n_lambda = stride
+            self.lengths = [int(x) for x in lengths]
+            self._lam = (lam, lengths)
+            st = lib().pmf_solve_schedules(self._h, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                           lengths.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), stride, strm)
+            _check(st, "pmf_solve_schedules")
+            return
         lam = np.ascontiguousarray(lambdas, np.int32)
         if lam.ndim == 1:
             lam = np.broadcast_to(lam, (len(self.inst_image), lam.shape[0])).copy()
         self.n_lambda = int(lam.shape[1])
+        self.lengths = [self.n_lambda] * len(self.inst_image)
         self._lam = lam
         st = lib().pmf_solve_schedule(self._h, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                      self.n_lambda, _stream_ptr(stream if stream is not None else self.stream))
+                                      self.n_lambda, strm)
         _check(st, "pmf_solve_schedule")
 
     def sync(self, check: bool = True):
@@ -293,7 +316,7 @@ class Batch:
         return out
 
     def flows(self, inst: int) -> np.ndarray:
-        out = np.empty(self.n_lambda, np.int64)
+        out = np.empty(self.lengths[inst], np.int64)
         _check(lib().pmf_get_flows(self._h, int(inst), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
                "pmf_get_flows")
         return out
@@ -316,21 +339,22 @@ class Batch:
         return {"f_h": a[0], "f_v": a[1], "f_s": a[2], "f_t": a[3]}
 
     def cuts(self, inst: int, out=None) -> np.ndarray:
-        """All masks of an instance, [n_lambda, H, W] (numpy host array, or a
-        contiguous uint8 CUDA tensor for a device copy)."""
+        """All masks of an instance, [its schedule length, H, W] (numpy host
+        array, or a contiguous uint8 CUDA tensor for a device copy)."""
         H, W = self.shapes[self.inst_image[inst]]
+        m = self.lengths[inst]
         if out is None:
-            out = np.empty((self.n_lambda, H, W), np.uint8)
+            out = np.empty((m, H, W), np.uint8)
         try:
             import torch
             if isinstance(out, torch.Tensor):
                 assert out.is_cuda and out.dtype == torch.uint8 and out.is_contiguous()
-                assert out.numel() == self.n_lambda * H * W
+                assert out.numel() == m * H * W
                 _check(lib().pmf_get_cuts(self._h, int(inst), ctypes.c_void_p(out.data_ptr()), 1), "pmf_get_cuts")
                 return out
         except ImportError:
             pass
-        assert out.dtype == np.uint8 and out.flags.c_contiguous and out.size == self.n_lambda * H * W
+        assert out.dtype == np.uint8 and out.flags.c_contiguous and out.size == m * H * W
         _check(lib().pmf_get_cuts(self._h, int(inst), ctypes.c_void_p(out.ctypes.data), 0), "pmf_get_cuts")
         return out
 
@@ -394,14 +418,11 @@ def batch_from_workload(wl, device: int = 0, stream=None, device_inputs: bool = 
 
 
 def solve_workload(wl, device: int = 0, check: bool = True, **tuning):
-    """Solve every instance of a Workload in one batch.  All instances must have
-    schedules of the same length.  Returns (per-instance statuses, list of
-    (flows [m], masks [m, H, W]))."""
-    lens = {len(i.lambdas) for i in wl.instances}
-    if len(lens) != 1:
-        raise ValueError("solve_workload needs schedules of one length")
+    """Solve every instance of a Workload in one batch (schedules may differ in
+    length).  Returns (per-instance statuses, list of (flows [m_i], masks
+    [m_i, H, W]))."""
     b = batch_from_workload(wl, device=device, **tuning)
-    b.solve(np.stack([i.lambdas for i in wl.instances]))
+    b.solve([np.asarray(i.lambdas) for i in wl.instances])
     st = b.sync(check=check)
     res = []
     for i in range(len(wl.instances)):

@@ -91,6 +91,65 @@ def test_batching_modes_agree(P):
             assert np.array_equal(f, base[s][0]) and np.array_equal(m, base[s][1])
 
 
+@pytest.mark.parametrize("pieces", [[1, 7], [3, 5], [2, 1, 5], [5, 2, 1], [1, 1, 1, 1, 4]])
+def test_uneven_pieces_agree(P, pieces):
+    """Schedules cut into pieces of different lengths (one launch with
+    per-instance schedule lengths) give the unsplit results."""
+    wl = _synthetic(14, 58, 95, 2, 8)
+    base = _solve(P, wl)
+    split = _solve(P, wl.split_pieces(pieces))
+    n = len(pieces)
+    for s in range(len(wl.instances)):
+        assert [len(split[s * n + j][0]) for j in range(n)] == pieces
+        f = np.concatenate([split[s * n + j][0] for j in range(n)])
+        m = np.concatenate([split[s * n + j][1] for j in range(n)])
+        assert np.array_equal(f, base[s][0]) and np.array_equal(m, base[s][1])
+
+
+def test_ragged_schedules_status_codes_and_reuse(P):
+    """pmf_solve_schedules: argument checks, entries past an instance's length
+    ignored, and a batch alternating between ragged and uniform schedules."""
+    wl = _synthetic(15, 36, 50, 3, 6)
+    b = P.batch_from_workload(wl)
+    lam = np.stack([i.lambdas for i in wl.instances]).astype(np.int32)
+    lengths = np.array([6, 2, 4], np.int32)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    L = P.lib()
+    padded = lam.copy()
+    padded[1, 2:] = 1                     # past instance 1's length: ignored even though decreasing
+    assert L.pmf_solve_schedules(b._h, padded.ctypes.data_as(i32p), lengths.ctypes.data_as(i32p), 6, None) == 0
+    b.lengths = [int(x) for x in lengths]
+    assert b.sync(check=False) == [P.PMF_OK] * 3
+    for i in range(3):
+        of, om = oracle.grid_solve(36, 50, wl.images[0].w_h, wl.images[0].w_v, wl.instances[i].src0,
+                                   wl.instances[i].slope, wl.instances[i].sink, lam[i, :lengths[i]])
+        assert np.array_equal(b.flows(i), of) and np.array_equal(b.cuts(i), om)
+    with pytest.raises(P.PmfError) as e:  # beyond the instance's own schedule
+        b.get_flow(1, 2)
+    assert e.value.status == P.PMF_ERR_INVALID_ARG
+    bad = lengths.copy()
+    bad[0] = 7                            # longer than the stride
+    assert L.pmf_solve_schedules(b._h, lam.ctypes.data_as(i32p), bad.ctypes.data_as(i32p), 6, None) \
+        == P.PMF_ERR_INVALID_ARG
+    bad[0] = 0
+    assert L.pmf_solve_schedules(b._h, lam.ctypes.data_as(i32p), bad.ctypes.data_as(i32p), 6, None) \
+        == P.PMF_ERR_INVALID_ARG
+    assert L.pmf_solve_schedules(b._h, lam.ctypes.data_as(i32p), None, 6, None) == P.PMF_ERR_INVALID_ARG
+    dec = lam.copy()
+    dec[2, 1], dec[2, 2] = dec[2, 2], dec[2, 1]
+    assert L.pmf_solve_schedules(b._h, dec.ctypes.data_as(i32p), lengths.ctypes.data_as(i32p), 6, None) \
+        == P.PMF_ERR_NOT_MONOTONE
+    # back to one length for all, then ragged again through the binding
+    b.solve(lam)
+    b.sync()
+    assert all(len(b.flows(i)) == 6 for i in range(3))
+    b.solve([lam[0, :1], lam[1], lam[2, :3]])
+    b.sync()
+    assert [len(b.flows(i)) for i in range(3)] == [1, 6, 3]
+    assert b.cuts(2).shape == (3, 36, 50)
+    b.close()
+
+
 def test_repeated_solves_and_device_inputs(P):
     wl = _synthetic(5, 50, 77, 2, 5)
     b = P.batch_from_workload(wl)

@@ -48,6 +48,23 @@ def test_random_small_grids(pmf, shape, tile_h, push_order):
     check_workload(pmf, wl, tile_h=tile_h, push_order=push_order)
 
 
+@pytest.mark.parametrize("push_order", [0, 1])
+def test_ragged_schedules_mixed_sizes(pmf, push_order):
+    """One launch over grids of different sizes whose schedules differ in
+    length (1 to 9 lambdas): every flow and mask against the oracle."""
+    rng = np.random.default_rng(77)
+    wl = inputs.Workload("ragged")
+    for j, (H, W) in enumerate([(9, 33), (17, 65), (40, 70), (3, 5), (33, 97)]):
+        g = inputs.random_grid(H, W, rng, wmax=20, tmax=40, p_zero=0.2, n_lambda=int(rng.integers(1, 10)), lam_max=30)
+        wl.images.append(g.images[0])
+        for _ in range(2):
+            inst = g.instances[0]
+            m = int(rng.integers(1, len(inst.lambdas) + 1))
+            wl.instances.append(inputs.Instance(j, inst.src0, inst.slope, inst.sink, inst.lambdas[:m]))
+    assert len({len(i.lambdas) for i in wl.instances}) > 1
+    check_workload(pmf, wl, tile_h=4, push_order=push_order)
+
+
 @pytest.mark.parametrize("mode", ["persistent", "persistent-nograph", "rounds"])
 def test_modes_on_synthetic_image(pmf, mode):
     rng = np.random.default_rng(3)
