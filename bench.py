@@ -34,9 +34,10 @@ from paper_1509_06004_b300 import inputs  # noqa: E402
 METRIC = "pixel-solves/s and solves/s, batched vs per-solve launch; serving p50/p99 latency"
 UNIT = "pixel-solves/s"
 # algorithmic bytes per pixel of one worker-kernel visit: a push/relabel visit
-# covers a 30 x tile_h tile, a global-relabel visit a 30 x 32 strip
+# covers a 30 x tile_h tile, a global-relabel or warm-start visit a 30 x 32 strip
 PR_BYTES_PER_PX = 48    # reads e, h, rt, fR, fD, w_h, w_v (28 B); writes e, h, rt, fR, fD (20 B)
 BFS_BYTES_PER_PX = 33   # reads e, rt, fR, fD, h, w_h, w_v (28 B); writes h (4 B) and the mask (1 B)
+WARM_BYTES_PER_PX = 24  # reads e, rt, h, slope (16 B); writes e, rt (8 B)
 BFS_STRIP_PX = 30 * 32
 L2_FLUSH_BYTES = 512 << 20
 
@@ -221,7 +222,7 @@ def run_ours(args, rank, world, dev):
     # are checked by the tests; here only the invariants the solver certifies
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    worker_ms, solve_ms, pr_v, bfs_v = [], [], 0, 0
+    worker_ms, solve_ms, pr_v, bfs_v, warm_v = [], [], 0, 0, 0
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -242,6 +243,7 @@ def run_ours(args, rank, world, dev):
                 stt = b.stats(i)
                 pr_v += stt["pr_visits"]
                 bfs_v += stt["bfs_visits"]
+                warm_v += stt["warm_visits"]
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -252,7 +254,8 @@ def run_ours(args, rank, world, dev):
     solves_s = world * wl.n_solves * args.steps / total_s
 
     # roofline of the dominant kernel (the persistent worker)
-    alg_bytes = (PR_BYTES_PER_PX * pr_v * tile_px + BFS_BYTES_PER_PX * bfs_v * BFS_STRIP_PX) / args.steps
+    alg_bytes = (PR_BYTES_PER_PX * pr_v * tile_px + BFS_BYTES_PER_PX * bfs_v * BFS_STRIP_PX
+                 + WARM_BYTES_PER_PX * warm_v * BFS_STRIP_PX) / args.steps
     wk_ms = float(np.mean(worker_ms))
     achieved = alg_bytes / (wk_ms / 1e3) / 1e9
     peaks = {}
@@ -277,7 +280,8 @@ def run_ours(args, rank, world, dev):
                      "kernel": "worker_kernel (persistent push/relabel + global relabel)",
                      "worker_ms": wk_ms, "alg_bytes_per_launch": alg_bytes,
                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                     "visits_per_launch": {"push_relabel_tiles": pr_v / args.steps, "bfs_strips": bfs_v / args.steps}},
+                     "visits_per_launch": {"push_relabel_tiles": pr_v / args.steps, "bfs_strips": bfs_v / args.steps,
+                                           "warm_start_strips": warm_v / args.steps}},
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
     }

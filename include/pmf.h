@@ -136,10 +136,11 @@ typedef struct {
 /* Per-instance counters of the last solve (pmf_get_stats). */
 typedef struct {
     int64_t pr_visits;       /* push/relabel tile visits */
-    int64_t bfs_visits;      /* global-relabel (BFS) tile visits */
+    int64_t bfs_visits;      /* global-relabel (BFS) strip visits */
     int64_t global_relabels; /* BFS epochs */
     int32_t lambdas_done;    /* schedule entries solved */
     int32_t status;          /* pmf_status of the instance */
+    int64_t warm_visits;     /* strip visits raising the source capacities at a lambda step */
 } pmf_stats;
 
 /* Bytes of device workspace a batch of this shape needs (host-only call). */

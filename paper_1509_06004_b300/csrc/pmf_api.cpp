@@ -804,6 +804,7 @@ pmf_status pmf_get_stats(pmf_batch *b, int32_t inst, pmf_stats *out) {
     out->global_relabels = (int64_t)s.epochs;
     out->lambdas_done = s.k;
     out->status = s.status;
+    out->warm_visits = (int64_t)s.warm_visits;
     return PMF_OK;
 }
 

@@ -25,7 +25,9 @@ enum Plane { P_E = 0, P_H = 1, P_RT = 2, P_FR = 3, P_FD = 4, P_SRC0 = 5, P_SLOPE
 // instance phases
 // PH_FWD: after a certified step of an instance whose caller swapped s and t,
 // the pass that finds the pixels reachable from excess (its cut)
-enum Phase { PH_BFS = 0, PH_PR = 1, PH_DONE = 2, PH_FWD = 3 };
+// PH_WARM: at the start of each later lambda step, the strip pass that raises
+// the source capacities (GGT warm start) and counts the tiles left active
+enum Phase { PH_BFS = 0, PH_PR = 1, PH_DONE = 2, PH_FWD = 3, PH_WARM = 4 };
 // tile queue states
 enum TState { T_IDLE = 0, T_QUEUED = 1, T_RUNNING = 2, T_DIRTY = 3 };
 // global error flags; GE_INTERNAL_MASK marks a broken scheduler invariant, after
@@ -68,6 +70,7 @@ struct alignas(128) InstState {  // mutable during a solve
     alignas(128) int32_t outstanding, active, dmax, pad3_;
     unsigned long long flow;         // int64 two's complement: total flow into t
     unsigned long long pr_visits, bfs_visits;
+    unsigned long long warm_visits;  // strip visits of the warm-start phases
 };
 
 static_assert(sizeof(InstState) % 16 == 0, "InstState array elements must stay 16-byte aligned");
@@ -87,7 +90,7 @@ enum TraceKind { TR_BFS_START = 0, TR_STEP_DONE = 1, TR_PR_START = 2, TR_DONE = 
 constexpr int TRACE_CAP = 1 << 16;
 
 struct TileState {
-    int32_t state, epoch, lam, active;
+    int32_t state, epoch, pad_, active;   // pad_: unused
 };
 
 // the queue counters sit on separate 128-byte lines: head is hit by every pop,

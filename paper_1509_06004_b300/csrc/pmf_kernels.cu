@@ -280,6 +280,12 @@ __device__ bool transition_once(const Params &P, int inst) {
         if (S->status != PMF_OK) {
             S->phase = PH_DONE;
             atomicAdd(&P.g->inst_done, 1);
+        } else if (phase == PH_WARM) {         // the step's first push/relabel phase
+            S->phase = PH_PR;
+            S->pr_mark = S->pr_visits;
+            S->want_bfs = 0;
+            mode = 3;
+            trace(P, inst, TR_PR_START, S);
         } else if (phase == PH_PR) {           // start a global relabel
             S->dmax = 0;
             S->epoch = S->epoch + 1;
@@ -308,9 +314,8 @@ __device__ bool transition_once(const Params &P, int inst) {
                     atomicAdd(&P.g->inst_done, 1);
                     trace(P, inst, TR_DONE, S);
                 } else {
-                    S->phase = PH_PR;
-                    S->pr_mark = S->pr_visits;
-                    S->want_bfs = 0;
+                    // raise the source capacities to the next lambda, strip by strip
+                    S->phase = PH_WARM;
                     mode = 1;
                 }
             } else if ((long long)(visits - S->step_mark) > P.max_visits_per_tile * (long long)D.n_tiles) {
@@ -330,14 +335,17 @@ __device__ bool transition_once(const Params &P, int inst) {
     }
     mode = __shfl_sync(FULL_MASK, mode, 0);
     if (!mode) return false;
-    // the phase's parameters are published before any of its tiles can run
-    const int n = (mode == 2) ? count_active_tiles(P, D) : D.n_tiles;
+    // the phase's parameters are published before any of its tiles can run;
+    // a step's first push/relabel phase (mode 3) queues the tiles that the
+    // raise left active, with the budget of a phase over all tiles
+    const int n = (mode == 2 || mode == 3) ? count_active_tiles(P, D) : D.n_tiles;
+    const int n_budget = mode == 3 ? D.n_tiles : n;
     if (lane == 0 && S->phase == PH_PR) {
         // a push/relabel phase may spend relabel_pct% of the tiles it starts
         // with (at least 4 visits) before the next global relabel: when only
         // a few tiles hold active pixels, stranded excess is otherwise pushed
         // back and forth between them long before a relabel removes it
-        const long long bud = (long long)P.relabel_pct * n / 100;
+        const long long bud = (long long)P.relabel_pct * n_budget / 100;
         S->pr_budget = (int)(bud < 4 ? 4 : bud);
         // labels far above every exact distance of the last relabel belong
         // to excess that keeps climbing without reaching t: park it until
@@ -354,7 +362,7 @@ __device__ bool transition_once(const Params &P, int inst) {
     __syncwarp();
     // a relabel or forward pass works on strips (their leader tiles are
     // queued); push/relabel on tiles
-    enqueue_tiles(P, inst, D, mode == 2, S->phase == PH_BFS || S->phase == PH_FWD);
+    enqueue_tiles(P, inst, D, mode >= 2, S->phase == PH_BFS || S->phase == PH_FWD || S->phase == PH_WARM);
     int last = 0;
     if (lane == 0) {
         __threadfence();
@@ -506,7 +514,6 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
     int *base = P.planes + D.plane_off;
     int *E = base + P_E * PS, *Hh = base + P_H * PS, *RT = base + P_RT * PS;
     int *FR = base + P_FR * PS, *FD = base + P_FD * PS;
-    const int *SLOPE = base + P_SLOPE * PS;
     const int *WH = P.img + D.img_off;
     const int *WV = WH + PS;
     const long long c_start = P.trace ? clock64() : 0;
@@ -535,25 +542,6 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
         const int c = lane == 0 ? 0 : 1;
 #pragma unroll
         for (int i = 0; i < TH; ++i) S.f0[c][i] = fr[i];
-    }
-
-    // GGT warm start: raise the source capacities to lambda_k (Section 2.1's
-    // monotone case keeps the old flow valid); the newly available source
-    // capacity becomes excess, and the part the sink arc can take is sent there
-    TileState *TS = P.tiles + g;
-    const int tl = ldv(&TS->lam);
-    if (tl < kcur) {
-        const int *L = P.lambdas + (size_t)inst * P.max_lambdas;
-        const int dl = L[kcur] - L[tl];
-#pragma unroll
-        for (int i = 0; i < TH; ++i) {
-            const int sl = own ? __ldg(SLOPE + (size_t)(T.y0 + i) * pitch + T.X) : 0;
-            e[i] += sl * dl;
-            const int m = min(e[i], rt[i]);
-            e[i] -= m;
-            rt[i] -= m;
-        }
-        if (lane == 0) TS->lam = kcur;
     }
 
     // rows above and below the tile
@@ -844,6 +832,88 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
         const unsigned long long v = atomicAdd(&P.ist[inst].pr_visits, 1ULL) + 1;
         const long long since = (long long)(v - *(volatile unsigned long long *)&P.ist[inst].pr_mark);
         if (since >= (long long)*(volatile int *)&P.ist[inst].pr_budget) P.ist[inst].want_bfs = 1;
+    }
+}
+
+// --------------------------------------------------------------------------
+// warm-start visit: GGT's raise of the source capacities from lambda_{k-1} to
+// lambda_k (Section 2.1's monotone case keeps the flow valid) for one strip:
+// the new source capacity becomes excess, the part the sink arc can take goes
+// to t, and each member tile's count of active pixels (excess and a finite
+// label) is set for the step's first push/relabel phase.  Nothing else of the
+// instance runs in this phase, so every value is written directly.
+// --------------------------------------------------------------------------
+template <int TH>
+__device__ void warm_visit(const Params &P, int g, int inst, const DevInst &D, int kcur) {
+    constexpr int BR = BFS_ROWS;
+    constexpr int SPAN = BR / TH;
+    const TileGeo T = tile_geo(g, D, TH);
+    const int lane = T.lane;
+    const bool own = T.inb && !T.ghost;
+    const int pitch = D.pitch;
+    const size_t PS = (size_t)D.rows * pitch;
+    int *base = P.planes + D.plane_off;
+    int *E = base + P_E * PS, *RT = base + P_RT * PS;
+    const int *Hh = base + P_H * PS, *SLOPE = base + P_SLOPE * PS;
+    const int *L = P.lambdas + (size_t)inst * P.max_lambdas;
+    const int dl = __ldg(L + kcur) - __ldg(L + kcur - 1);
+    long long sent = 0;
+    unsigned live = 0;   // bit i: row i's pixel is active after the raise
+    constexpr int LB = 8;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BR; c0 += LB) {
+        int e[LB], rt[LB], h[LB], sl[LB];
+#pragma unroll
+        for (int j = 0; j < LB; ++j) {
+            const int y = T.y0 + c0 + j;
+            const bool ok = own && y < D.rows;
+            const size_t idx = (size_t)y * pitch + T.X;
+            e[j] = ok ? __ldcg(E + idx) : 0;
+            rt[j] = ok ? __ldcg(RT + idx) : 0;
+            h[j] = ok ? __ldcg(Hh + idx) : HINF;
+            sl[j] = ok ? __ldg(SLOPE + idx) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < LB; ++j) {
+            const int y = T.y0 + c0 + j;
+            const bool ok = own && y < D.rows;
+            const int add = sl[j] * dl;
+            const int m = min(e[j] + add, rt[j]);
+            const int en = e[j] + add - m;
+            if (ok && add) {
+                const size_t idx = (size_t)y * pitch + T.X;
+                __stcg(E + idx, en);
+                if (m) __stcg(RT + idx, rt[j] - m);
+            }
+            sent += ok ? m : 0;
+            live |= (ok && en > 0 && h[j] < HINF) ? (1u << (c0 + j)) : 0u;
+        }
+    }
+    int cnt[SPAN];
+    constexpr unsigned TMASK = (TH == 32) ? 0xffffffffu : ((1u << TH) - 1u);
+#pragma unroll
+    for (int j = 0; j < SPAN; ++j)
+        cnt[j] = (int)__reduce_add_sync(FULL_MASK, (unsigned)__popc(live & (TMASK << (j * TH))));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sent += __shfl_down_sync(FULL_MASK, sent, o);
+    __threadfence();
+    __syncwarp();
+    int delta = 0;
+    if (lane < SPAN && T.ty + lane < D.tiles_y) {
+        int mine = 0;
+#pragma unroll
+        for (int j = 0; j < SPAN; ++j) mine = (j == lane) ? cnt[j] : mine;
+        int *act = &P.tiles[g + lane * D.tiles_x].active;
+        const int old = ldv(act);
+        *(volatile int *)act = mine;
+        delta = mine - old;
+    }
+#pragma unroll
+    for (int o = SPAN / 2; o > 0; o >>= 1) delta += __shfl_down_sync(FULL_MASK, delta, o);
+    if (lane == 0) {
+        if (delta) atomicAdd(&P.ist[inst].active, delta);
+        if (sent) atomicAdd(&P.ist[inst].flow, (unsigned long long)sent);
+        atomicAdd(&P.ist[inst].warm_visits, 1ULL);
     }
 }
 
@@ -1266,7 +1336,7 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_ker
         unsigned nb = 0;
         // a relabel item must be a strip's leader tile: anything else means a
         // push/relabel item outlived its phase, which the phase changes rule out
-        const bool strip = phase == PH_BFS || phase == PH_FWD;
+        const bool strip = phase == PH_BFS || phase == PH_FWD || phase == PH_WARM;
         const bool stray = strip && ((g - D.tile_base) / D.tiles_x) % (BFS_ROWS / TH) != 0;
         if (stray && lane == 0) atomicOr(&P.g->err, GE_PHASE);
         if (status == PMF_OK && phase == PH_PR) pr_visit<TH, PO>(P, S, g, inst, D, k, requeue, nb);
@@ -1274,6 +1344,7 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_ker
             bfs_visit<TH, false>(P, S, g, inst, D, epoch, k, requeue, nb);
         else if (status == PMF_OK && phase == PH_FWD && !stray)
             bfs_visit<TH, true>(P, S, g, inst, D, epoch, k, requeue, nb);
+        else if (status == PMF_OK && phase == PH_WARM && !stray) warm_visit<TH>(P, g, inst, D, k);
         __threadfence();
         __syncwarp();
         if (prof) {
@@ -1371,7 +1442,7 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
         TileState t;
         t.state = lead ? T_QUEUED : T_IDLE;
         t.epoch = 0;
-        t.lam = 0;
+        t.pad_ = 0;
         t.active = 0;
         P.tiles[g] = t;
         // every relabel strip of every instance is queued for the first relabel
@@ -1399,6 +1470,7 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
         s.flow = 0;
         s.pr_visits = 0;
         s.bfs_visits = 0;
+        s.warm_visits = 0;
         P.ist[i] = s;
     }
     if (t0 == 0) {

@@ -83,7 +83,7 @@ TRACE_EVENTS = {0: "relabel", 1: "step-done", 2: "push-relabel", 3: "done", 4: "
 class Stats(ctypes.Structure):
     _fields_ = [("pr_visits", ctypes.c_int64), ("bfs_visits", ctypes.c_int64),
                 ("global_relabels", ctypes.c_int64), ("lambdas_done", ctypes.c_int32),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("warm_visits", ctypes.c_int64)]
 
 
 _lib = None
