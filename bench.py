@@ -372,20 +372,30 @@ def e2e(args, wl, b, lam, dev, stream, pmf, world):
         t = torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
         return t.numpy()
     imgs = [(pinned(im.w_h), pinned(im.w_v)) for im in wl.images]
-    terms = [(pinned(i.src0), pinned(i.slope), pinned(i.sink)) for i in wl.instances]
+    # the pieces of one seed share its terminal arrays: uploaded once, then
+    # copied on the device (pmf_copy_terminals)
+    first, src_of = {}, []
+    for i, inst in enumerate(wl.instances):
+        key = (inst.image, id(inst.src0), id(inst.slope), id(inst.sink))
+        src_of.append(first.setdefault(key, i))
+    terms = [(pinned(inst.src0), pinned(inst.slope), pinned(inst.sink)) if src_of[i] == i else None
+             for i, inst in enumerate(wl.instances)]
     outs = []
     for inst in wl.instances:
         im = wl.images[inst.image]
         outs.append(torch.empty((len(inst.lambdas), im.H, im.W), dtype=torch.uint8).pin_memory().numpy())
     flows = np.empty((len(wl.instances), lam.shape[1]), np.int64)
-    h2d = sum(a.nbytes + c.nbytes for a, c in imgs) + sum(x.nbytes for t in terms for x in t) + lam.nbytes
+    h2d = sum(a.nbytes + c.nbytes for a, c in imgs) + sum(x.nbytes for t in terms if t for x in t) + lam.nbytes
     d2h = sum(o.nbytes for o in outs) + flows.nbytes
 
     def one():
         for i, (a, c) in enumerate(imgs):
             b.set_capacities(i, a, c)
         for i, t in enumerate(terms):
-            b.set_terminals(i, *t)
+            if t is None:
+                b.copy_terminals(i, src_of[i])
+            else:
+                b.set_terminals(i, *t)
         b.solve(lam, stream=stream)
         b.sync()
         for i in range(len(wl.instances)):

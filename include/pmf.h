@@ -178,6 +178,15 @@ PMF_API pmf_status pmf_set_capacities(pmf_batch *b, int32_t image, const int32_t
 PMF_API pmf_status pmf_set_terminals(pmf_batch *b, int32_t inst, const int32_t *src0,
                              const int32_t *slope, const int32_t *sink, int on_device);
 
+/* Instance dst takes the terminal capacities last set for instance src (both
+ * instances of the same image), with src's validation result: one
+ * device-to-device copy queued on the batch's stream, no host transfer.  For
+ * one problem split into several instances, e.g. a seed's schedule cut into
+ * pieces that run side by side (Section 3.1's supergraph of (seed, lambda)
+ * problems).  PMF_ERR_INVALID_ARG for an index out of range or instances of
+ * different images; dst == src does nothing. */
+PMF_API pmf_status pmf_copy_terminals(pmf_batch *b, int32_t dst, int32_t src);
+
 /* Section 3.2's s-t swap: the caller may solve an instance with s and t
  * exchanged, passing its sink capacities as src0 (slope 0) and its source
  * capacities at one lambda as sink through pmf_set_terminals (pairwise

@@ -511,6 +511,27 @@ pmf_status pmf_set_capacities(pmf_batch *b, int32_t image, const int32_t *w_h, c
     return host_flags_status(f);
 }
 
+pmf_status pmf_copy_terminals(pmf_batch *b, int32_t dst, int32_t src) {
+    if (!b || dst < 0 || dst >= b->desc.n_inst || src < 0 || src >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
+    if (b->inst_image[dst] != b->inst_image[src]) return PMF_ERR_INVALID_ARG;
+    if (dst == src) return PMF_OK;
+    DeviceGuard dg(b->device);
+    if (b->in_flight) { cudaEventSynchronize(b->done); b->in_flight = false; }
+    const DevInst &ds = b->dinst[src], &dd = b->dinst[dst];
+    const size_t ps = (size_t)ds.rows * ds.pitch;
+    // src0, slope and ct are consecutive planes of an instance: one copy, and
+    // the validation flags with them (pmf_sync reports them as for src)
+    int32_t *planes = (int32_t *)(b->ws + b->L.inst_planes);
+    int32_t *flags = (int32_t *)(b->ws + b->L.inst_flags);
+    cudaStream_t s = b->setup_stream;
+    cudaError_t e = cudaMemcpyAsync(planes + dd.plane_off + P_SRC0 * ps, planes + ds.plane_off + P_SRC0 * ps,
+                                    3 * ps * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(flags + dst, flags + src, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    b->solved = false;
+    return cuda_err(e);
+}
+
 pmf_status pmf_set_cut_rule(pmf_batch *b, int32_t inst, int32_t rule) {
     if (!b || inst < 0 || inst >= b->desc.n_inst || (rule != 0 && rule != 1)) return PMF_ERR_INVALID_ARG;
     DeviceGuard dg(b->device);

@@ -35,7 +35,7 @@ PMF_MAX_PAIRWISE = (1 << 28) - 1
 
 # every entry point declared in include/pmf.h
 EXPORTS = ["pmf_workspace_size", "pmf_create_batch", "pmf_set_tuning", "pmf_get_tuning",
-           "pmf_set_capacities", "pmf_set_terminals", "pmf_solve_schedule", "pmf_solve_schedules", "pmf_sync",
+           "pmf_set_capacities", "pmf_set_terminals", "pmf_copy_terminals", "pmf_solve_schedule", "pmf_solve_schedules", "pmf_sync",
            "pmf_get_cut", "pmf_get_flow", "pmf_get_cuts", "pmf_get_flows", "pmf_get_timing",
            "pmf_get_stats", "pmf_get_trace", "pmf_get_profile", "pmf_get_mask_layout",
            "pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error",
@@ -110,6 +110,7 @@ def lib(path: str | None = None):
             L.pmf_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
             L.pmf_set_capacities.argtypes = [vp, i32, vp, vp, ctypes.c_int]
             L.pmf_set_terminals.argtypes = [vp, i32, vp, vp, vp, ctypes.c_int]
+            L.pmf_copy_terminals.argtypes = [vp, i32, i32]
             L.pmf_solve_schedule.argtypes = [vp, i32p, i32, vp]
             L.pmf_solve_schedules.argtypes = [vp, i32p, i32p, i32, vp]
             L.pmf_sync.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
@@ -237,6 +238,11 @@ class Batch:
         st = lib().pmf_set_terminals(self._h, int(inst), args[0][0], args[1][0], args[2][0], args[0][1])
         self._pin2 = [a[2] for a in args]
         _check(st, "pmf_set_terminals")
+
+    def copy_terminals(self, dst: int, src: int):
+        """Instance dst takes instance src's terminal capacities (same image),
+        copied on the device (pmf_copy_terminals)."""
+        _check(lib().pmf_copy_terminals(self._h, int(dst), int(src)), "pmf_copy_terminals")
 
     def set_tuning(self, **kw):
         t = Tuning()
@@ -412,8 +418,15 @@ def batch_from_workload(wl, device: int = 0, stream=None, device_inputs: bool = 
         if device_inputs else (lambda a: a)
     for i, im in enumerate(wl.images):
         b.set_capacities(i, conv(im.w_h), conv(im.w_v))
+    # pieces of one problem (the same terminal arrays) are uploaded once
+    first = {}
     for i, inst in enumerate(wl.instances):
-        b.set_terminals(i, conv(inst.src0), conv(inst.slope), conv(inst.sink))
+        key = (inst.image, id(inst.src0), id(inst.slope), id(inst.sink))
+        if key in first:
+            b.copy_terminals(i, first[key])
+        else:
+            b.set_terminals(i, conv(inst.src0), conv(inst.slope), conv(inst.sink))
+            first[key] = i
     return b
 
 

@@ -78,4 +78,6 @@ def test_null_arguments_are_rejected_without_gpu():
     assert L.pmf_sync(None, None) == pmf.PMF_ERR_INVALID_ARG
     assert L.pmf_get_flow(None, 0, 0, None) == pmf.PMF_ERR_INVALID_ARG
     assert L.pmf_get_flow_arcs(None, 0, None, None, None, None) == pmf.PMF_ERR_INVALID_ARG
+    assert L.pmf_copy_terminals(None, 0, 0) == pmf.PMF_ERR_INVALID_ARG
+    assert L.pmf_solve_schedules(None, None, None, 1, None) == pmf.PMF_ERR_INVALID_ARG
     L.pmf_destroy_batch(None)

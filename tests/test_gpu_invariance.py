@@ -106,6 +106,29 @@ def test_uneven_pieces_agree(P, pieces):
         assert np.array_equal(f, base[s][0]) and np.array_equal(m, base[s][1])
 
 
+def test_copied_terminals_equal_uploaded_ones(P):
+    """Pieces of one seed share its terminal arrays, so the binding uploads
+    them once and copies them on the device (pmf_copy_terminals); the results
+    equal those of separate uploads."""
+    wl = _synthetic(16, 44, 70, 2, 6).split_segments(3)
+    shared = _solve(P, wl)
+    sep = inputs.Workload("sep", wl.images, [inputs.Instance(i.image, i.src0.copy(), i.slope.copy(), i.sink.copy(),
+                                                             i.lambdas) for i in wl.instances])
+    _same(shared, _solve(P, sep))
+    b = P.batch_from_workload(_synthetic(17, 20, 30, 2, 2))
+    L = P.lib()
+    assert L.pmf_copy_terminals(b._h, 0, 2) == P.PMF_ERR_INVALID_ARG
+    assert L.pmf_copy_terminals(b._h, -1, 0) == P.PMF_ERR_INVALID_ARG
+    assert L.pmf_copy_terminals(b._h, 1, 1) == P.PMF_OK
+    b.close()
+    two = inputs.Workload("two", _synthetic(18, 20, 30, 1, 2).images + _synthetic(19, 24, 30, 1, 2).images, [])
+    two.instances = [inputs.Instance(0, *([np.zeros((20, 30), np.int32)] * 3), np.array([1, 2], np.int32)),
+                     inputs.Instance(1, *([np.zeros((24, 30), np.int32)] * 3), np.array([1, 2], np.int32))]
+    b = P.batch_from_workload(two)
+    assert L.pmf_copy_terminals(b._h, 1, 0) == P.PMF_ERR_INVALID_ARG   # different images
+    b.close()
+
+
 def test_ragged_schedules_status_codes_and_reuse(P):
     """pmf_solve_schedules: argument checks, entries past an instance's length
     ignored, and a batch alternating between ragged and uniform schedules."""
