@@ -228,14 +228,23 @@ PMF_API pmf_status pmf_solve_schedules(pmf_batch *b, const int32_t *lambdas, con
  * instance's pmf_status.  Returns PMF_OK iff every instance converged. */
 PMF_API pmf_status pmf_sync(pmf_batch *b, pmf_status *per_instance);
 
+/* Which instances have finished, without waiting: while a solve runs, the
+ * kernel flags each instance in mapped host memory as it finishes, so
+ * done[i] = 1 (host array of n_inst bytes, may be NULL) for a finished one and
+ * *n_done (may be NULL) counts them; after pmf_sync every instance of the
+ * solve is reported.  A finished instance that converged can be read at once
+ * (pmf_get_cut(s), pmf_get_flow(s)) while the others still run: its results are
+ * final.  Its status, and any failure, come with pmf_sync. */
+PMF_API pmf_status pmf_poll(pmf_batch *b, uint8_t *done, int32_t *n_done);
+
 /* Mask of solve (inst, k): H*W bytes, 1 = source (foreground) side.
  * on_device = 1: mask is a device pointer (copied in stream order, then the
- * stream is synchronised), 0: host pointer.  PMF_ERR_NOT_READY before pmf_sync
- * of a finished solve. */
+ * stream is synchronised), 0: host pointer.  PMF_ERR_NOT_READY until the
+ * instance has finished and converged (pmf_poll) or after a failed one. */
 PMF_API pmf_status pmf_get_cut(pmf_batch *b, int32_t inst, int32_t k, uint8_t *mask, int on_device);
 
 /* Maximum flow value of solve (inst, k) (Section 2: equal to the minimum cut
- * cost), after pmf_sync. */
+ * cost), once the instance has finished (pmf_poll, pmf_sync). */
 PMF_API pmf_status pmf_get_flow(pmf_batch *b, int32_t inst, int32_t k, int64_t *flow);
 
 /* Every mask of instance inst: n_lambda * H * W bytes, [k][y][x], as one copy

@@ -207,7 +207,8 @@ struct pmf_batch {
     long long *flows_h = nullptr;
     Globals *glob_h = nullptr;
     DevInst *dinst_h = nullptr;
-    size_t pinned_bytes[5] = {0, 0, 0, 0, 0};
+    int32_t *done_h = nullptr;             // written by the kernel: 1 + status of each finished instance
+    size_t pinned_bytes[6] = {0, 0, 0, 0, 0, 0};
     // captured graph
     cudaGraphExec_t gexec = nullptr;
     bool graph_valid = false;
@@ -380,9 +381,10 @@ pmf_status pmf_create_batch(const pmf_batch_desc *desc, void *dev_workspace, siz
     b->pinned_bytes[2] = sizeof(long long) * nl;
     b->pinned_bytes[3] = sizeof(Globals);
     b->pinned_bytes[4] = sizeof(DevInst) * desc->n_inst;
-    void **dst[5] = {(void **)&b->lam_h, (void **)&b->ist_h, (void **)&b->flows_h, (void **)&b->glob_h,
-                     (void **)&b->dinst_h};
-    for (int j = 0; j < 5 && e == cudaSuccess; ++j) {
+    b->pinned_bytes[5] = sizeof(int32_t) * desc->n_inst;
+    void **dst[6] = {(void **)&b->lam_h, (void **)&b->ist_h, (void **)&b->flows_h, (void **)&b->glob_h,
+                     (void **)&b->dinst_h, (void **)&b->done_h};
+    for (int j = 0; j < 6 && e == cudaSuccess; ++j) {
         *dst[j] = pinned_arena().alloc(b->pinned_bytes[j]);
         if (!*dst[j]) e = cudaErrorMemoryAllocation;
     }
@@ -411,6 +413,12 @@ pmf_status pmf_create_batch(const pmf_batch_desc *desc, void *dev_workspace, siz
     P.g = (Globals *)(b->ws + L.globals);
     P.img_flags = (const int32_t *)(b->ws + L.img_flags);
     P.inst_flags = (int32_t *)(b->ws + L.inst_flags);
+    {
+        // pinned host memory is addressable from the device (unified addressing)
+        void *dp = nullptr;
+        P.done_flags = cudaHostGetDevicePointer(&dp, b->done_h, 0) == cudaSuccess ? (int32_t *)dp : nullptr;
+        std::memset(b->done_h, 0, b->pinned_bytes[5]);
+    }
     P.ring_mask = (unsigned long long)(L.ring_cap - 1);
     P.n_inst = desc->n_inst;
     P.max_lambdas = desc->max_lambdas;
@@ -595,6 +603,7 @@ static pmf_status solve_impl(pmf_batch *b, const int32_t *lambdas, const int32_t
     DeviceGuard dg(b->device);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (b->in_flight) { cudaEventSynchronize(b->done); b->in_flight = false; }
+    std::memset(b->done_h, 0, b->pinned_bytes[5]);
     // lambda table [n_inst][max_lambdas] in pinned staging (the last value
     // repeated past an instance's length)
     for (int i = 0; i < b->desc.n_inst; ++i)
@@ -716,11 +725,38 @@ pmf_status pmf_sync(pmf_batch *b, pmf_status *per_instance) {
     return all;
 }
 
+// Whether an instance's results can be read: after pmf_sync from the copied
+// instance states; while the solve runs, once the kernel has flagged the
+// instance finished and converged (its results are then final in device
+// memory; flows are read from there).
+enum Ready { NOT_READY = 0, READY_SYNCED, READY_IN_FLIGHT };
+static Ready ready(const pmf_batch *b, int inst, int k_needed) {
+    if (!b->in_flight) {
+        if (!b->solved) return NOT_READY;
+        const InstState &s = b->ist_h[inst];
+        return s.status == PMF_OK && s.k >= k_needed ? READY_SYNCED : NOT_READY;
+    }
+    const int f = *(volatile const int32_t *)(b->done_h + inst);
+    return f == 1 + PMF_OK ? READY_IN_FLIGHT : NOT_READY;
+}
+
+pmf_status pmf_poll(pmf_batch *b, uint8_t *done, int32_t *n_done) {
+    if (!b) return PMF_ERR_INVALID_ARG;
+    int n = 0;
+    for (int i = 0; i < b->desc.n_inst; ++i) {
+        const bool d = b->in_flight ? *(volatile const int32_t *)(b->done_h + i) != 0
+                                    : (b->solved && b->ist_h[i].phase == PH_DONE);
+        if (done) done[i] = d ? 1 : 0;
+        n += d;
+    }
+    if (n_done) *n_done = n;
+    return PMF_OK;
+}
+
 pmf_status pmf_get_cut(pmf_batch *b, int32_t inst, int32_t k, uint8_t *mask, int on_device) {
     if (!b || !mask || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
-    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
-    if (k < 0 || k >= b->n_lam[inst]) return PMF_ERR_INVALID_ARG;
-    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k <= k) return PMF_ERR_NOT_READY;
+    if (k < 0 || k >= std::max(b->n_lam[inst], 1)) return PMF_ERR_INVALID_ARG;
+    if (ready(b, inst, k + 1) == NOT_READY) return PMF_ERR_NOT_READY;
     DeviceGuard dg(b->device);
     const DevInst &d = b->dinst[inst];
     const char *src = b->ws + b->L.masks + d.mask_off + (size_t)k * d.rows * d.pitch;
@@ -731,19 +767,32 @@ pmf_status pmf_get_cut(pmf_batch *b, int32_t inst, int32_t k, uint8_t *mask, int
     return cuda_err(e);
 }
 
+// the flow values of a ready instance, from the host mirror or, while the
+// solve runs, from device memory
+static pmf_status read_flows(pmf_batch *b, int inst, Ready r, int64_t *out, int k0, int n) {
+    const size_t at = (size_t)inst * b->desc.max_lambdas + k0;
+    if (r == READY_SYNCED) {
+        for (int k = 0; k < n; ++k) out[k] = b->flows_h[at + k];
+        return PMF_OK;
+    }
+    DeviceGuard dg(b->device);
+    cudaError_t e = cudaMemcpyAsync(out, b->ws + b->L.flows + sizeof(long long) * at, sizeof(int64_t) * n,
+                                    cudaMemcpyDeviceToHost, b->cap_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap_stream);
+    return cuda_err(e);
+}
+
 pmf_status pmf_get_flow(pmf_batch *b, int32_t inst, int32_t k, int64_t *flow) {
     if (!b || !flow || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
-    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
-    if (k < 0 || k >= b->n_lam[inst]) return PMF_ERR_INVALID_ARG;
-    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k <= k) return PMF_ERR_NOT_READY;
-    *flow = b->flows_h[(size_t)inst * b->desc.max_lambdas + k];
-    return PMF_OK;
+    if (k < 0 || k >= std::max(b->n_lam[inst], 1)) return PMF_ERR_INVALID_ARG;
+    const Ready r = ready(b, inst, k + 1);
+    if (r == NOT_READY) return PMF_ERR_NOT_READY;
+    return read_flows(b, inst, r, flow, k, 1);
 }
 
 pmf_status pmf_get_cuts(pmf_batch *b, int32_t inst, uint8_t *masks, int on_device) {
     if (!b || !masks || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
-    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
-    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->n_lam[inst]) return PMF_ERR_NOT_READY;
+    if (ready(b, inst, b->n_lam[inst]) == NOT_READY) return PMF_ERR_NOT_READY;
     DeviceGuard dg(b->device);
     const DevInst &d = b->dinst[inst];
     // all lambdas in one 3-D copy: source slices rows x pitch, destination H x W
@@ -759,10 +808,9 @@ pmf_status pmf_get_cuts(pmf_batch *b, int32_t inst, uint8_t *masks, int on_devic
 
 pmf_status pmf_get_flows(pmf_batch *b, int32_t inst, int64_t *flows) {
     if (!b || !flows || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
-    if (b->in_flight || !b->solved) return PMF_ERR_NOT_READY;
-    if (b->ist_h[inst].status != PMF_OK || b->ist_h[inst].k < b->n_lam[inst]) return PMF_ERR_NOT_READY;
-    for (int k = 0; k < b->n_lam[inst]; ++k) flows[k] = b->flows_h[(size_t)inst * b->desc.max_lambdas + k];
-    return PMF_OK;
+    const Ready r = ready(b, inst, b->n_lam[inst]);
+    if (r == NOT_READY) return PMF_ERR_NOT_READY;
+    return read_flows(b, inst, r, flows, 0, b->n_lam[inst]);
 }
 
 pmf_status pmf_get_flow_arcs(pmf_batch *b, int32_t inst, int32_t *f_h, int32_t *f_v, int32_t *f_s,
@@ -853,6 +901,7 @@ void pmf_destroy_batch(pmf_batch *b) {
     pinned_arena().release(b->flows_h, b->pinned_bytes[2]);
     pinned_arena().release(b->glob_h, b->pinned_bytes[3]);
     pinned_arena().release(b->dinst_h, b->pinned_bytes[4]);
+    pinned_arena().release(b->done_h, b->pinned_bytes[5]);
     delete b;
 }
 

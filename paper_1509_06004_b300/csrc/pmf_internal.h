@@ -129,6 +129,7 @@ struct Params {
     Globals *g;
     const int32_t *img_flags;    // [n_images] validation flags of set_capacities
     int32_t *inst_flags;         // [n_inst] validation flags of set_terminals
+    int32_t *done_flags;         // [n_inst] host-mapped: 1 + status once an instance is finished (or nullptr)
     unsigned long long ring_mask;
     int32_t n_inst, n_tiles_total, max_lambdas, sweeps;
     int32_t n_leads_total, chain_push;   // chain_push: push order of the sweeps (pmf_tuning.push_order)

@@ -266,6 +266,14 @@ __device__ void trace(const Params &P, int inst, int event, volatile InstState *
     P.trace[i] = e;
 }
 
+// An instance has reached PH_DONE: tell the host (a word in mapped host
+// memory), after everything the instance wrote (its masks and flow values,
+// made visible at device scope by the visits' fences) is ordered before it.
+__device__ void mark_done(const Params &P, int inst, int status) {
+    __threadfence_system();
+    if (P.done_flags) *(volatile int32_t *)(P.done_flags + inst) = 1 + status;
+}
+
 // One phase change.  Returns true when the items it queued had all finished
 // before it let go of its guard: the caller is then the instance's last
 // finisher again and must run the next phase change itself.
@@ -280,6 +288,7 @@ __device__ bool transition_once(const Params &P, int inst) {
         if (S->status != PMF_OK) {
             S->phase = PH_DONE;
             atomicAdd(&P.g->inst_done, 1);
+            mark_done(P, inst, S->status);
         } else if (phase == PH_WARM) {         // the step's first push/relabel phase
             S->phase = PH_PR;
             S->pr_mark = S->pr_visits;
@@ -312,6 +321,7 @@ __device__ bool transition_once(const Params &P, int inst) {
                 if (k + 1 >= D.n_lambda) {
                     S->phase = PH_DONE;
                     atomicAdd(&P.g->inst_done, 1);
+                    mark_done(P, inst, PMF_OK);
                     trace(P, inst, TR_DONE, S);
                 } else {
                     // raise the source capacities to the next lambda, strip by strip
@@ -322,6 +332,7 @@ __device__ bool transition_once(const Params &P, int inst) {
                 S->status = PMF_ERR_NOT_CONVERGED;
                 S->phase = PH_DONE;
                 atomicAdd(&P.g->inst_done, 1);
+                mark_done(P, inst, PMF_ERR_NOT_CONVERGED);
                 trace(P, inst, TR_NOT_CONVERGED, S);
             } else {
                 S->phase = PH_PR;

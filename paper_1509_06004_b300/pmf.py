@@ -35,7 +35,7 @@ PMF_MAX_PAIRWISE = (1 << 28) - 1
 
 # every entry point declared in include/pmf.h
 EXPORTS = ["pmf_workspace_size", "pmf_create_batch", "pmf_set_tuning", "pmf_get_tuning",
-           "pmf_set_capacities", "pmf_set_terminals", "pmf_copy_terminals", "pmf_solve_schedule", "pmf_solve_schedules", "pmf_sync",
+           "pmf_set_capacities", "pmf_set_terminals", "pmf_copy_terminals", "pmf_solve_schedule", "pmf_solve_schedules", "pmf_sync", "pmf_poll",
            "pmf_get_cut", "pmf_get_flow", "pmf_get_cuts", "pmf_get_flows", "pmf_get_timing",
            "pmf_get_stats", "pmf_get_trace", "pmf_get_profile", "pmf_get_mask_layout",
            "pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error",
@@ -114,6 +114,7 @@ def lib(path: str | None = None):
             L.pmf_solve_schedule.argtypes = [vp, i32p, i32, vp]
             L.pmf_solve_schedules.argtypes = [vp, i32p, i32p, i32, vp]
             L.pmf_sync.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+            L.pmf_poll.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
             L.pmf_get_cut.argtypes = [vp, i32, i32, vp, ctypes.c_int]
             L.pmf_get_flow.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_int64)]
             L.pmf_get_stats.argtypes = [vp, i32, ctypes.POINTER(Stats)]
@@ -289,6 +290,14 @@ class Batch:
         st = lib().pmf_solve_schedule(self._h, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                       self.n_lambda, strm)
         _check(st, "pmf_solve_schedule")
+
+    def poll(self) -> np.ndarray:
+        """Finished instances of the running (or last) solve, without waiting:
+        a bool array; finished ones that converged can be read already."""
+        done = np.zeros(len(self.inst_image), np.uint8)
+        n = ctypes.c_int32(0)
+        _check(lib().pmf_poll(self._h, ctypes.c_void_p(done.ctypes.data), ctypes.byref(n)), "pmf_poll")
+        return done.astype(bool)
 
     def sync(self, check: bool = True):
         per = (ctypes.c_int * len(self.inst_image))()

@@ -129,6 +129,35 @@ def test_copied_terminals_equal_uploaded_ones(P):
     b.close()
 
 
+def test_poll_reads_finished_instances_during_the_solve(P):
+    """Instances read as soon as pmf_poll reports them finished (while larger
+    ones still run) equal the results after pmf_sync and the oracle's."""
+    import torch
+    small = _synthetic(20, 24, 40, 3, 4)
+    big = _synthetic(21, 200, 300, 2, 12)
+    wl = inputs.Workload("mix", small.images + big.images, list(small.instances))
+    for inst in big.instances:
+        wl.instances.append(inputs.Instance(1, inst.src0, inst.slope, inst.sink, inst.lambdas))
+    b = P.batch_from_workload(wl)
+    early = {}
+    b.solve([i.lambdas for i in wl.instances])
+    ev = torch.cuda.Event()
+    ev.record(torch.cuda.current_stream())
+    while len(early) < len(wl.instances):
+        fresh = [i for i in np.nonzero(b.poll())[0] if i not in early]
+        for i in fresh:
+            early[i] = (b.flows(i), b.cuts(i))
+        if not fresh and ev.query():
+            break
+    assert b.sync() == [P.PMF_OK] * len(wl.instances)
+    assert b.poll().all()
+    ref = oracle.solve_workload(wl, instances=list(early))
+    for (i, (f, m)), (of, om) in zip(early.items(), ref):
+        assert np.array_equal(f, b.flows(i)) and np.array_equal(m, b.cuts(i))
+        assert np.array_equal(f, of) and np.array_equal(m, om)
+    b.close()
+
+
 def test_ragged_schedules_status_codes_and_reuse(P):
     """pmf_solve_schedules: argument checks, entries past an instance's length
     ignored, and a batch alternating between ragged and uniform schedules."""
