@@ -1142,6 +1142,11 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     int rounds = 0;
     for (int it = 0; it < 4 * BR; ++it) {
         ++rounds;
+        // A pass down and a pass up a column leave every vertical constraint
+        // met (on a path, one sweep each way gives the exact distances), and
+        // the two row passes do the same for the horizontal ones.  So a round
+        // whose row passes change nothing ends at the fixpoint: only their
+        // changes are tracked.
         bool ch = false;
         {   // vertical: a pass down and a pass up the column, 8 rows at a time
             constexpr int CH = 8;
@@ -1155,7 +1160,6 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
                 for (int j = 0; j < CH; ++j) {
                     const bool bb = ((aU >> (c0 + j)) & 1u) && up + 1 < d[j];
                     d[j] = bb ? up + 1 : d[j];
-                    ch |= bb;
                     up = d[j];
                 }
 #pragma unroll
@@ -1171,7 +1175,6 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
                 for (int j = CH - 1; j >= 0; --j) {
                     const bool bb = ((aD >> (c0 + j)) & 1u) && dn + 1 < d[j];
                     d[j] = bb ? dn + 1 : d[j];
-                    ch |= bb;
                     dn = d[j];
                 }
 #pragma unroll

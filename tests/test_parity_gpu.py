@@ -48,6 +48,29 @@ def test_random_small_grids(pmf, shape, tile_h, push_order):
     check_workload(pmf, wl, tile_h=tile_h, push_order=push_order)
 
 
+@pytest.mark.parametrize("case", ["repeated", "zero-slope", "from-zero"])
+def test_warm_start_edge_schedules(pmf, case):
+    """Schedules that make the warm-start pass a no-op or near one: repeated
+    lambdas (no raise), instances without any lambda dependence, a schedule
+    starting at lambda = 0; against the oracle."""
+    rng = np.random.default_rng({"repeated": 81, "zero-slope": 82, "from-zero": 83}[case])
+    wl = inputs.Workload(case)
+    for j, (H, W) in enumerate([(23, 47), (40, 33)]):
+        g = inputs.random_grid(H, W, rng, wmax=20, tmax=40, p_zero=0.2, n_lambda=3, lam_max=30)
+        wl.images.append(g.images[0])
+        inst = g.instances[0]
+        slope = np.zeros_like(inst.slope) if case == "zero-slope" else inst.slope
+        if case == "repeated":
+            lam = np.array([5, 5, 9, 9, 9, 20], np.int32)
+        elif case == "from-zero":
+            lam = np.array([0, 0, 1, 2, 30], np.int32)
+        else:
+            lam = np.array([3, 10, 10, 30], np.int32)
+        wl.instances.append(inputs.Instance(j, inst.src0, slope, inst.sink, lam))
+    check_workload(pmf, wl, tile_h=4, push_order=1)
+    check_workload(pmf, wl, tile_h=8, push_order=0)
+
+
 @pytest.mark.parametrize("push_order", [0, 1])
 def test_ragged_schedules_mixed_sizes(pmf, push_order):
     """One launch over grids of different sizes whose schedules differ in
