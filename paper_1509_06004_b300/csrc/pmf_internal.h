@@ -16,8 +16,10 @@ constexpr int TILE_IN = 30;                // interior columns of a tile: lanes 
 constexpr int ROW_ALIGN = 16;              // rows padded so tile heights 4/8/16 divide them
 constexpr int32_t HINF = 0x3fffffff;       // label of a pixel that cannot reach t
 constexpr int BFS_ROWS = 32;               // rows of a relabel strip (a column of tiles)
-// per relabel strip: 6 arc masks, 3 border residuals and 32 label rows, 32 lanes each
-constexpr int STRIP_REC_WORDS = (9 + BFS_ROWS) * 32;
+// per relabel strip, 32 lanes each: 6 arc masks, 3 border residuals, 32 label
+// rows, and the member tiles' active counts (lane j: tile j) as last written
+constexpr int RW_CNT = 9 + BFS_ROWS;
+constexpr int STRIP_REC_WORDS = (RW_CNT + 1) * 32;
 constexpr int N_INST_PLANES = 8;           // e, h, rt, fR, fD, src0, slope, ct
 constexpr int N_IMG_PLANES = 2;            // w_h, w_v
 enum Plane { P_E = 0, P_H = 1, P_RT = 2, P_FR = 3, P_FD = 4, P_SRC0 = 5, P_SLOPE = 6, P_CT = 7 };

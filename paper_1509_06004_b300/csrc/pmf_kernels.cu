@@ -868,6 +868,10 @@ __device__ void warm_visit(const Params &P, int g, int inst, const DevInst &D, i
     const int *Hh = base + P_H * PS, *SLOPE = base + P_SLOPE * PS;
     const int *L = P.lambdas + (size_t)inst * P.max_lambdas;
     const int dl = __ldg(L + kcur) - __ldg(L + kcur - 1);
+    // the member tiles' counts as last written, kept in the strip record
+    int32_t *cnt_rec = P.strip_cache + (size_t)(D.lead_base + (T.ty / SPAN) * D.tiles_x + T.tx) * STRIP_REC_WORDS
+                       + RW_CNT * 32;
+    const int cnt_old = lane < SPAN ? ldv(cnt_rec + lane) : 0;
     long long sent = 0;
     unsigned live = 0;   // bit i: row i's pixel is active after the raise
     constexpr int LB = 8;
@@ -914,10 +918,9 @@ __device__ void warm_visit(const Params &P, int g, int inst, const DevInst &D, i
         int mine = 0;
 #pragma unroll
         for (int j = 0; j < SPAN; ++j) mine = (j == lane) ? cnt[j] : mine;
-        int *act = &P.tiles[g + lane * D.tiles_x].active;
-        const int old = ldv(act);
-        *(volatile int *)act = mine;
-        delta = mine - old;
+        *(volatile int *)&P.tiles[g + lane * D.tiles_x].active = mine;
+        __stcg(cnt_rec + lane, mine);
+        delta = mine - cnt_old;
     }
 #pragma unroll
     for (int o = SPAN / 2; o > 0; o >>= 1) delta += __shfl_down_sync(FULL_MASK, delta, o);
@@ -966,6 +969,12 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     bool vX = own_valid;
     if (lane == 0) vX = T.tx > 0 && ldv(&P.tiles[g - 1].epoch) == epoch;
     if (lane == 31) vX = T.tx < D.tiles_x - 1 && ldv(&P.tiles[g + 1].epoch) == epoch;
+    // the member tiles' active counts as last written (lane j: tile j), kept in
+    // the strip record so that replacing them needs no read after the relaxation;
+    // the previous writer may be on another SM, so the read bypasses L1
+    const int32_t *cnt_rec = P.strip_cache + (size_t)(D.lead_base + (T.ty / SPAN) * D.tiles_x + T.tx) * STRIP_REC_WORDS
+                             + RW_CNT * 32;
+    const int cnt_old = (!FWD && lane < SPAN) ? ldv(cnt_rec + lane) : 0;
     __threadfence();
 
     // This strip's record: the arc bit masks and border residuals its first
@@ -1271,12 +1280,9 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
         int mine = 0;
 #pragma unroll
         for (int j = 0; j < SPAN; ++j) mine = (j == lane) ? cnt[j] : mine;
-        int *act = &P.tiles[g + lane * D.tiles_x].active;
-        // the previous count may have been written from another SM: read it
-        // past L1 (a stale line would corrupt the instance's total)
-        const int old = ldv(act);
-        *(volatile int *)act = mine;
-        delta = mine - old;
+        *(volatile int *)&P.tiles[g + lane * D.tiles_x].active = mine;
+        __stcg(REC + RW_CNT * 32 + lane, mine);
+        delta = mine - cnt_old;
     }
 #pragma unroll
     for (int o = SPAN / 2; o > 0; o >>= 1) delta += __shfl_down_sync(FULL_MASK, delta, o);
@@ -1460,7 +1466,13 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
         t.active = 0;
         P.tiles[g] = t;
         // every relabel strip of every instance is queued for the first relabel
-        if (lead) P.ring[__ldg(&P.inst[lo].lead_base) + (ty / span) * tiles_x + tx] = (int)g;
+        if (lead) {
+            const size_t strip = (size_t)__ldg(&P.inst[lo].lead_base) + (size_t)(ty / span) * tiles_x + tx;
+            P.ring[strip] = (int)g;
+            // the strip record's copy of its tiles' active counts starts with them, at 0
+            int32_t *cnt = P.strip_cache + strip * STRIP_REC_WORDS + RW_CNT * 32;
+            for (int j = 0; j < span; ++j) cnt[j] = 0;
+        }
     }
     for (size_t i = t0; i < (size_t)P.n_inst; i += stride) {
         const DevInst D = P.inst[i];
