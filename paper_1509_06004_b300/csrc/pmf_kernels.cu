@@ -51,6 +51,13 @@ __device__ __forceinline__ unsigned long long gtime_ns() {
     return t;
 }
 __device__ __forceinline__ int ldv(const int *p) { return *(const volatile int *)p; }
+// load with acquire semantics at device scope: every later load of this thread
+// sees what the writer wrote before its release (a fence, then this word)
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ unsigned long long ldv64(const unsigned long long *p) {
     return *(const volatile unsigned long long *)p;
 }
@@ -962,20 +969,23 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     const long long c_start = P.trace ? clock64() : 0;
 
     // labels of a neighbouring strip count only once it has been visited in
-    // this relabel epoch (otherwise they are left over from push/relabel)
-    const bool own_valid = ldv(&TS->epoch) == epoch;
-    const bool vT = T.ty >= SPAN && ldv(&P.tiles[g - vstride].epoch) == epoch;
-    const bool vB = T.ty + SPAN < D.tiles_y && ldv(&P.tiles[g + vstride].epoch) == epoch;
+    // this relabel epoch (otherwise they are left over from push/relabel).  A
+    // visit stores its labels and record, fences, then stores its epoch; the
+    // epochs are read with acquire loads, so the reads of those labels and of
+    // this strip's own record that follow see them (each lane acquires the
+    // epochs whose data it reads)
+    const bool own_valid = ld_acquire(&TS->epoch) == epoch;
+    const bool vT = T.ty >= SPAN && ld_acquire(&P.tiles[g - vstride].epoch) == epoch;
+    const bool vB = T.ty + SPAN < D.tiles_y && ld_acquire(&P.tiles[g + vstride].epoch) == epoch;
     bool vX = own_valid;
-    if (lane == 0) vX = T.tx > 0 && ldv(&P.tiles[g - 1].epoch) == epoch;
-    if (lane == 31) vX = T.tx < D.tiles_x - 1 && ldv(&P.tiles[g + 1].epoch) == epoch;
+    if (lane == 0) vX = T.tx > 0 && ld_acquire(&P.tiles[g - 1].epoch) == epoch;
+    if (lane == 31) vX = T.tx < D.tiles_x - 1 && ld_acquire(&P.tiles[g + 1].epoch) == epoch;
     // the member tiles' active counts as last written (lane j: tile j), kept in
     // the strip record so that replacing them needs no read after the relaxation;
     // the previous writer may be on another SM, so the read bypasses L1
     const int32_t *cnt_rec = P.strip_cache + (size_t)(D.lead_base + (T.ty / SPAN) * D.tiles_x + T.tx) * STRIP_REC_WORDS
                              + RW_CNT * 32;
     const int cnt_old = (!FWD && lane < SPAN) ? ldv(cnt_rec + lane) : 0;
-    __threadfence();
 
     // This strip's record: the arc bit masks and border residuals its first
     // visit of the epoch found (arcs do not change during a relabel phase),
