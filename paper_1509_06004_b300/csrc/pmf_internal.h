@@ -17,7 +17,8 @@ constexpr int ROW_ALIGN = 16;              // rows padded so tile heights 4/8/16
 constexpr int32_t HINF = 0x3fffffff;       // label of a pixel that cannot reach t
 constexpr int BFS_ROWS = 32;               // rows of a relabel strip (a column of tiles)
 // per relabel strip, 32 lanes each: 6 arc masks, 3 border residuals, 32 label
-// rows, and the member tiles' active counts (lane j: tile j) as last written
+// rows (used by the forward pass), and the member tiles' active counts (lane
+// j: tile j) as last written
 constexpr int RW_CNT = 9 + BFS_ROWS;
 constexpr int STRIP_REC_WORDS = (RW_CNT + 1) * 32;
 constexpr int N_INST_PLANES = 8;           // e, h, rt, fR, fD, src0, slope, ct

@@ -989,9 +989,11 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
 
     // This strip's record: the arc bit masks and border residuals its first
     // visit of the epoch found (arcs do not change during a relabel phase),
-    // and its labels as its last visit left them.  Words [k][lane]:
+    // and, for the forward pass, its labels as its last visit left them (a
+    // relabel keeps its labels in the label plane only).  Words [k][lane]:
     // k = 0..5 masks R, D, U, E, Q, V; 6..8 residuals up from row 0, down
-    // into row 0, up into the last row; 9 + i the label of row i.
+    // into row 0, up into the last row; 9 + i the label of row i;
+    // RW_CNT the member tiles' active counts.
     int32_t *REC = P.strip_cache + (size_t)(D.lead_base + (T.ty / SPAN) * D.tiles_x + T.tx) * STRIP_REC_WORDS;
     // the forward pass keeps its labels in the records only (the distances to
     // t in the label plane stay for push/relabel), so it reads neighbouring
@@ -1015,8 +1017,9 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     }
     if (own_valid) {
         // a second visit in this epoch: masks and residuals from the record,
-        // labels of this strip's own columns from the record, the ghost
-        // columns' from the neighbouring strips' labels
+        // labels of this strip's own columns as its last visit left them (the
+        // label plane; the forward pass: the record), the ghost columns' from
+        // the neighbouring strips' labels
         bR = (unsigned)__ldcg(REC + 0 * 32 + lane);
         bD = (unsigned)__ldcg(REC + 1 * 32 + lane);
         bU = (unsigned)__ldcg(REC + 2 * 32 + lane);
@@ -1030,7 +1033,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
             if constexpr (FWD) hT = __ldcg(REC_T + (9 + BR - 1) * 32 + lane);
             else hT = __ldcg(Hh + (size_t)(T.y0 - 1) * pitch + T.X);
         }
-        constexpr int LH = 16;
+        constexpr int LH = 32;
 #pragma unroll 1
         for (int c0 = 0; c0 < BR; c0 += LH) {
             int dv[LH];
@@ -1038,7 +1041,8 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
             for (int j = 0; j < LH; ++j) {
                 const int i = c0 + j;
                 const bool rowok = T.y0 + i < D.rows;
-                dv[j] = own ? __ldcg(REC + (9 + i) * 32 + lane) : (T.inb && rowok && vX) ? ghost_label(i) : HINF;
+                if constexpr (FWD) dv[j] = own ? __ldcg(REC + (9 + i) * 32 + lane) : (T.inb && rowok && vX) ? ghost_label(i) : HINF;
+                else dv[j] = (T.inb && rowok && (own || vX)) ? __ldcg(Hh + (size_t)(T.y0 + i) * pitch + T.X) : HINF;
             }
 #pragma unroll
             for (int j = 0; j < LH; ++j) {
@@ -1271,7 +1275,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
             M[idx] = di >= HINF ? 1 : 0;
             dm = di < HINF ? max(dm, di) : dm;
         }
-        if (own) __stcg(REC + (9 + i) * 32 + lane, di);
+        if (FWD && own) __stcg(REC + (9 + i) * 32 + lane, di);
         live |= di < HINF ? (1u << i) : 0u;
     }
     // active pixels (positive excess, finite label) of each member tile
