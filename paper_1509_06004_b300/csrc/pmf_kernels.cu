@@ -300,7 +300,7 @@ __device__ bool transition_once(const Params &P, int inst) {
             S->phase = PH_PR;
             S->pr_mark = S->pr_visits;
             S->want_bfs = 0;
-            mode = 3;
+            mode = 2;
             trace(P, inst, TR_PR_START, S);
         } else if (phase == PH_PR) {           // start a global relabel
             S->dmax = 0;
@@ -353,17 +353,14 @@ __device__ bool transition_once(const Params &P, int inst) {
     }
     mode = __shfl_sync(FULL_MASK, mode, 0);
     if (!mode) return false;
-    // the phase's parameters are published before any of its tiles can run;
-    // a step's first push/relabel phase (mode 3) queues the tiles that the
-    // raise left active, with the budget of a phase over all tiles
-    const int n = (mode == 2 || mode == 3) ? count_active_tiles(P, D) : D.n_tiles;
-    const int n_budget = mode == 3 ? D.n_tiles : n;
+    // the phase's parameters are published before any of its tiles can run
+    const int n = (mode == 2) ? count_active_tiles(P, D) : D.n_tiles;
     if (lane == 0 && S->phase == PH_PR) {
         // a push/relabel phase may spend relabel_pct% of the tiles it starts
         // with (at least 4 visits) before the next global relabel: when only
         // a few tiles hold active pixels, stranded excess is otherwise pushed
         // back and forth between them long before a relabel removes it
-        const long long bud = (long long)P.relabel_pct * n_budget / 100;
+        const long long bud = (long long)P.relabel_pct * n / 100;
         S->pr_budget = (int)(bud < 4 ? 4 : bud);
         // labels far above every exact distance of the last relabel belong
         // to excess that keeps climbing without reaching t: park it until
@@ -380,7 +377,7 @@ __device__ bool transition_once(const Params &P, int inst) {
     __syncwarp();
     // a relabel or forward pass works on strips (their leader tiles are
     // queued); push/relabel on tiles
-    enqueue_tiles(P, inst, D, mode >= 2, S->phase == PH_BFS || S->phase == PH_FWD || S->phase == PH_WARM);
+    enqueue_tiles(P, inst, D, mode == 2, S->phase == PH_BFS || S->phase == PH_FWD || S->phase == PH_WARM);
     int last = 0;
     if (lane == 0) {
         __threadfence();
