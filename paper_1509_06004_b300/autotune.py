@@ -35,8 +35,8 @@ SPACE = {
     "tile_h": [4, 8],
     "push_order": [0, 1],
     "sweeps": [2, 4, 8, 16],
-    "relabel_every": [200, 400, 800, 1600],
-    "label_slack": [4, 8, 16, 32],
+    "relabel_every": [200, 400, 800, 1600, 3200, 6400],
+    "label_slack": [2, 4, 8, 16, 32],
 }
 
 
