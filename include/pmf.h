@@ -115,6 +115,9 @@ typedef struct {
                                 and pixel from the sweep's starting state (default);
                                 1 = along columns and rows, so excess that arrives
                                 can move on in the same sweep */
+    int32_t relabel_extra;   /* tile visits every push/relabel phase may spend on top
+                                of relabel_every% of its tiles (default 0): more room
+                                for phases that start with few active tiles */
 } pmf_tuning;
 
 /* One instance phase change recorded on the device (tuning.trace = 1). */

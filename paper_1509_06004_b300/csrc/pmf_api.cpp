@@ -238,6 +238,7 @@ void apply_defaults(pmf_tuning *t) {
     if (t->label_slack == 0) t->label_slack = 16;
     if (t->label_slack < 0) t->label_slack = -1;
     if (t->push_order != 1) t->push_order = 0;
+    if (t->relabel_extra < 0) t->relabel_extra = 0;
 }
 
 // per-instance tile geometry for the current tile height; uploads the table
@@ -617,6 +618,7 @@ static pmf_status solve_impl(pmf_batch *b, const int32_t *lambdas, const int32_t
     b->P.label_slack = b->tune.label_slack < 0 ? 0 : b->tune.label_slack;
     b->P.chain_push = b->tune.push_order;
     b->P.relabel_pct = b->tune.relabel_every;
+    b->P.relabel_extra = b->tune.relabel_extra;
     b->P.max_visits_per_tile = b->tune.max_visits_per_tile;
     const bool geo_changed = (b->P.tile_h != b->tune.tile_h) || len_changed;
     if (geo_changed) {

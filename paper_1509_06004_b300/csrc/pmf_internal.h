@@ -137,6 +137,7 @@ struct Params {
     int32_t n_inst, n_tiles_total, max_lambdas, sweeps;
     int32_t n_leads_total, chain_push;   // chain_push: push order of the sweeps (pmf_tuning.push_order)
     int32_t relabel_pct, tile_h;
+    int32_t relabel_extra, pad_p_;   // relabel_extra: visits added to every phase's budget
     int32_t poll_ns, label_slack;
     long long max_visits_per_tile;
     long long stall_ns;          // a worker gives up after this long without progress

@@ -360,7 +360,7 @@ __device__ bool transition_once(const Params &P, int inst) {
         // with (at least 4 visits) before the next global relabel: when only
         // a few tiles hold active pixels, stranded excess is otherwise pushed
         // back and forth between them long before a relabel removes it
-        const long long bud = (long long)P.relabel_pct * n / 100;
+        const long long bud = (long long)P.relabel_pct * n / 100 + P.relabel_extra;
         S->pr_budget = (int)(bud < 4 ? 4 : bud);
         // labels far above every exact distance of the last relabel belong
         // to excess that keeps climbing without reaching t: park it until

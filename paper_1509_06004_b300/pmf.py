@@ -67,7 +67,8 @@ class Tuning(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("trace", ctypes.c_int32),
                 ("poll_ns", ctypes.c_int32), ("label_slack", ctypes.c_int32),
-                ("grid_blocks", ctypes.c_int32), ("push_order", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32), ("push_order", ctypes.c_int32),
+                ("relabel_extra", ctypes.c_int32)]
 
 
 class TraceEvent(ctypes.Structure):
