@@ -378,6 +378,13 @@ def test_status_codes(P):
     b.solve(lam)
     st = b.sync(check=False)
     assert st == [P.PMF_ERR_NOT_MONOTONE, P.PMF_ERR_OVERFLOW]
+    assert b.poll().all()                         # failed instances are finished too
+    with pytest.raises(P.PmfError) as e:          # ... but have nothing to read
+        b.get_flow(1, 0)
+    assert e.value.status == P.PMF_ERR_NOT_READY
+    b.copy_terminals(1, 0)                        # a copy carries the validation result
+    b.solve(lam)
+    assert b.sync(check=False) == [P.PMF_ERR_NOT_MONOTONE, P.PMF_ERR_NOT_MONOTONE]
     b.close()
     # workspace too small
     d, keep = P._desc([(32, 40)], [0], 3, 0)
