@@ -197,7 +197,8 @@ def run_ours(args, rank, world, dev):
     wl = WORKLOADS[args.workload](rank_seed(args.seed, rank))
     tuning0 = {k: v for k, v in (("tile_h", args.tile_h), ("sweeps", args.sweeps),
                                  ("relabel_every", args.relabel_every), ("label_slack", args.label_slack),
-                                 ("push_order", args.push_order), ("relabel_extra", args.relabel_extra)) if v}
+                                 ("push_order", args.push_order), ("relabel_extra", args.relabel_extra),
+                                 ("poll_ns", args.poll_ns)) if v}
     m = min(len(i.lambdas) for i in wl.instances)
     segments, tuning, mode_probe = resolve_mode(args, wl, dev, tuning0)
     args.mode = mode_name(segments, m)
@@ -271,7 +272,7 @@ def run_ours(args, rank, world, dev):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": dict(describe(wl, args.mode), tile=f"30x{tile_px // 30} (+2 mirrored columns)",
                        sweeps=b.tuning()["sweeps"], relabel_every_pct=b.tuning()["relabel_every"],
-                       relabel_extra=b.tuning()["relabel_extra"],
+                       relabel_extra=b.tuning()["relabel_extra"], poll_ns=b.tuning()["poll_ns"],
                        label_slack=b.tuning()["label_slack"],
                        l2="flushed between timed steps (512 MB write)",
                        parallelism=f"replicas x{world} (independent instances, no collective)"),
@@ -515,6 +516,7 @@ def main(argv=None):
     ap.add_argument("--sweeps", type=int, default=0)
     ap.add_argument("--relabel-every", type=int, default=0)
     ap.add_argument("--relabel-extra", type=int, default=0)
+    ap.add_argument("--poll-ns", type=int, default=0)
     ap.add_argument("--label-slack", type=int, default=0)
     ap.add_argument("--push-order", type=int, default=0)
     ap.add_argument("--per-solve-sample", type=int, default=10)

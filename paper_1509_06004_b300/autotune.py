@@ -12,8 +12,9 @@ instance count and schedule length:
 * ``tile_h`` (rows per tile), ``push_order`` (pushes from the sweep's starting
   state, or along columns and rows), ``sweeps`` (push/relabel sweeps per tile visit),
   ``relabel_every`` (visit budget of a push/relabel phase, percent of its
-  tiles), ``relabel_extra`` (visits added to every phase's budget) and
-  ``label_slack`` (parking threshold above the last exact distance).
+  tiles), ``relabel_extra`` (visits added to every phase's budget),
+  ``label_slack`` (parking threshold above the last exact distance) and
+  ``poll_ns`` (longest sleep of an idle warp between polls of its queue slot).
 
 ``tune`` times candidates on the GPU by coordinate descent inside a time
 budget; choices are cached in a JSON file keyed by (GPU name, workload class).
@@ -31,7 +32,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_PATH = os.path.join(HERE, "tuned.json")
 
-DEFAULTS = {"tile_h": 4, "sweeps": 8, "relabel_every": 800, "label_slack": 16, "push_order": 0, "relabel_extra": 0}
+DEFAULTS = {"tile_h": 4, "sweeps": 8, "relabel_every": 800, "label_slack": 16, "push_order": 0, "relabel_extra": 0,
+            "poll_ns": 256}
 SPACE = {
     "tile_h": [4, 8],
     "push_order": [0, 1],
@@ -39,6 +41,7 @@ SPACE = {
     "relabel_every": [200, 400, 800, 1600, 3200, 6400],
     "label_slack": [2, 4, 8, 16, 32],
     "relabel_extra": [0, 64, 256, 1024],
+    "poll_ns": [256, 1024, 4096],
 }
 
 
