@@ -200,11 +200,30 @@ PMF_API pmf_status pmf_copy_terminals(pmf_batch *b, int32_t dst, int32_t src);
  * that set after each certified step as the pixels reachable in the residual
  * graph from pixels holding excess (every minimum cut's source side contains
  * them, and they form one).  rule = 0 (default): the maximal source set of the
- * problem as given.  Takes effect at the next pmf_solve_schedule.  With rule 1
- * the sink capacities do not follow lambda, so a schedule of one lambda is the
- * intended use (a warm-started exchanged schedule would need falling sink
- * capacities).  PMF_ERR_INVALID_ARG for a bad instance or rule. */
+ * problem as given.  Takes effect at the next pmf_solve_schedule.  A
+ * warm-started exchanged schedule also needs the exchanged sink capacities to
+ * follow lambda: see pmf_set_slope_side.  PMF_ERR_INVALID_ARG for a bad
+ * instance or rule. */
 PMF_API pmf_status pmf_set_cut_rule(pmf_batch *b, int32_t inst, int32_t rule);
+
+/* Which terminal arcs follow lambda (Section 2.1's monotone case: the factors
+ * of lambda are all of one sign).  side = 0 (default): the source capacities
+ * rise, cs(p, lambda) = src0 + slope * lambda, and ct(p) = sink.  side = 1:
+ * the sink capacities fall, cs(p) = src0 and ct(p, lambda) = sink - slope *
+ * lambda; a solve then reports PMF_ERR_INVALID_ARG for the instance if some
+ * ct(p, lambda) of its schedule is negative.  Either way the maximal source
+ * sets grow with lambda, so the GGT warm start carries each step's flow and
+ * labels to the next: with side 1 a sink arc that carries more than its new
+ * capacity gives the surplus back to its pixel as excess.  Side 1 with
+ * pmf_set_cut_rule(1) solves an exchanged problem over a whole schedule: with
+ * s and t exchanged, the original source capacities src0 + slope * lambda
+ * become sink capacities, and they fall as lambda falls, so the exchanged
+ * problem runs the original schedule backwards, with parameter
+ * mu = lambda_last - lambda and sink = src0 + slope * lambda_last.  The
+ * pair capacities and the planes are unchanged; only the instance's arithmetic
+ * differs.  Takes effect at the next pmf_solve_schedule.  PMF_ERR_INVALID_ARG
+ * for a bad instance or side. */
+PMF_API pmf_status pmf_set_slope_side(pmf_batch *b, int32_t inst, int32_t side);
 
 /* Solve every instance at every lambda of its schedule.  lambdas is a host
  * array [n_inst][n_lambda] (n_lambda <= max_lambdas), nondecreasing along each

@@ -545,8 +545,22 @@ pmf_status pmf_set_cut_rule(pmf_batch *b, int32_t inst, int32_t rule) {
     if (!b || inst < 0 || inst >= b->desc.n_inst || (rule != 0 && rule != 1)) return PMF_ERR_INVALID_ARG;
     DeviceGuard dg(b->device);
     if (b->in_flight) { cudaEventSynchronize(b->done); b->in_flight = false; }
-    b->dinst[inst].cut_rule = rule;
-    b->dinst_h[inst].cut_rule = rule;
+    b->dinst[inst].cut_rule = (int16_t)rule;
+    b->dinst_h[inst].cut_rule = (int16_t)rule;
+    cudaStream_t s = b->setup_stream;
+    cudaError_t e = cudaMemcpyAsync(b->ws + b->L.dev_inst + sizeof(DevInst) * inst, &b->dinst_h[inst],
+                                    sizeof(DevInst), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_err(e);
+}
+
+pmf_status pmf_set_slope_side(pmf_batch *b, int32_t inst, int32_t side) {
+    if (!b || inst < 0 || inst >= b->desc.n_inst || (side != 0 && side != 1)) return PMF_ERR_INVALID_ARG;
+    DeviceGuard dg(b->device);
+    if (b->in_flight) { cudaEventSynchronize(b->done); b->in_flight = false; }
+    b->dinst[inst].slope_side = (int16_t)side;
+    b->dinst_h[inst].slope_side = (int16_t)side;
+    b->graph_valid = false;   // the worker kernel is chosen by whether any instance has side 1
     cudaStream_t s = b->setup_stream;
     cudaError_t e = cudaMemcpyAsync(b->ws + b->L.dev_inst + sizeof(DevInst) * inst, &b->dinst_h[inst],
                                     sizeof(DevInst), cudaMemcpyHostToDevice, s);
@@ -619,6 +633,8 @@ static pmf_status solve_impl(pmf_batch *b, const int32_t *lambdas, const int32_t
     b->P.chain_push = b->tune.push_order;
     b->P.relabel_pct = b->tune.relabel_every;
     b->P.relabel_extra = b->tune.relabel_extra;
+    b->P.any_sink_side = 0;
+    for (int i = 0; i < b->desc.n_inst; ++i) b->P.any_sink_side |= b->dinst[i].slope_side != 0;
     b->P.max_visits_per_tile = b->tune.max_visits_per_tile;
     const bool geo_changed = (b->P.tile_h != b->tune.tile_h) || len_changed;
     if (geo_changed) {

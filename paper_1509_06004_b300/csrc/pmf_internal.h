@@ -52,7 +52,8 @@ struct DevInst {                 // read-only during a solve
     int64_t img_off;             // int32 elements from the image-plane base
     int64_t mask_off;            // bytes from the mask base
     int32_t n_leads;             // relabel strips (tiles_x * ceil(tiles_y / strip_span))
-    int32_t cut_rule;            // 0: maximal source set; 1: s and t swapped by the caller (pmf_set_cut_rule)
+    int16_t cut_rule;            // 0: maximal source set; 1: s and t swapped by the caller (pmf_set_cut_rule)
+    int16_t slope_side;          // 0: cs = src0 + slope*lambda, ct = sink; 1: cs = src0, ct = sink - slope*lambda
 };
 
 // 16-byte aligned: the worker reads the first four fields with one 16-byte
@@ -137,7 +138,8 @@ struct Params {
     int32_t n_inst, n_tiles_total, max_lambdas, sweeps;
     int32_t n_leads_total, chain_push;   // chain_push: push order of the sweeps (pmf_tuning.push_order)
     int32_t relabel_pct, tile_h;
-    int32_t relabel_extra, pad_p_;   // relabel_extra: visits added to every phase's budget
+    int32_t relabel_extra;       // visits added to every phase's budget
+    int32_t any_sink_side;       // some instance's sink capacities fall with lambda (slope_side 1)
     int32_t poll_ns, label_slack;
     long long max_visits_per_tile;
     long long stall_ns;          // a worker gives up after this long without progress

@@ -851,14 +851,17 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
 }
 
 // --------------------------------------------------------------------------
-// warm-start visit: GGT's raise of the source capacities from lambda_{k-1} to
-// lambda_k (Section 2.1's monotone case keeps the flow valid) for one strip:
-// the new source capacity becomes excess, the part the sink arc can take goes
-// to t, and each member tile's count of active pixels (excess and a finite
-// label) is set for the step's first push/relabel phase.  Nothing else of the
-// instance runs in this phase, so every value is written directly.
+// warm-start visit: GGT's change of the terminal capacities from lambda_{k-1}
+// to lambda_k (Section 2.1's monotone case keeps the labels valid) for one
+// strip.  Rising source capacities: the new capacity becomes excess, and the
+// part the sink arc can take goes to t.  Falling sink capacities: the sink
+// arc's residual shrinks, and where the arc carried more than its new capacity
+// the surplus flow is taken back from t and becomes excess.  Either way each
+// member tile's count of active pixels (excess and a finite label) is set for
+// the step's first push/relabel phase.  Nothing else of the instance runs in
+// this phase, so every value is written directly.
 // --------------------------------------------------------------------------
-template <int TH>
+template <int TH, bool SINK>
 __device__ void warm_visit(const Params &P, int g, int inst, const DevInst &D, int kcur) {
     constexpr int BR = BFS_ROWS;
     constexpr int SPAN = BR / TH;
@@ -872,6 +875,9 @@ __device__ void warm_visit(const Params &P, int g, int inst, const DevInst &D, i
     const int *Hh = base + P_H * PS, *SLOPE = base + P_SLOPE * PS;
     const int *L = P.lambdas + (size_t)inst * P.max_lambdas;
     const int dl = __ldg(L + kcur) - __ldg(L + kcur - 1);
+    // which terminal arcs follow lambda (only kernels built for batches with
+    // falling sink capacities look)
+    const bool sink_side = SINK && __ldg(&P.inst[inst].slope_side) != 0;
     // the member tiles' counts as last written, kept in the strip record
     int32_t *cnt_rec = P.strip_cache + (size_t)(D.lead_base + (T.ty / SPAN) * D.tiles_x + T.tx) * STRIP_REC_WORDS
                        + RW_CNT * 32;
@@ -896,16 +902,37 @@ __device__ void warm_visit(const Params &P, int g, int inst, const DevInst &D, i
         for (int j = 0; j < LB; ++j) {
             const int y = T.y0 + c0 + j;
             const bool ok = own && y < D.rows;
-            const int add = sl[j] * dl;
-            const int m = min(e[j] + add, rt[j]);
-            const int en = e[j] + add - m;
-            if (ok && add) {
-                const size_t idx = (size_t)y * pitch + T.X;
-                __stcg(E + idx, en);
-                if (m) __stcg(RT + idx, rt[j] - m);
+            const int d = sl[j] * dl;
+            if constexpr (SINK) {
+                // the source capacity rises by up or the sink capacity falls
+                // by dn; a sink arc left carrying more than its capacity gives
+                // the surplus back to its pixel; then the part of the excess
+                // the sink arc can take goes to t
+                const int up = sink_side ? 0 : d, dn = sink_side ? d : 0;
+                const int back = max(dn - rt[j], 0);
+                const int rt1 = max(rt[j] - dn, 0);
+                const int e1 = e[j] + up + back;
+                const int m = min(e1, rt1);
+                const int en = e1 - m, rtn = rt1 - m;
+                if (ok && d) {
+                    const size_t idx = (size_t)y * pitch + T.X;
+                    if (en != e[j]) __stcg(E + idx, en);
+                    if (rtn != rt[j]) __stcg(RT + idx, rtn);
+                }
+                sent += ok ? m - back : 0;
+                live |= (ok && en > 0 && h[j] < HINF) ? (1u << (c0 + j)) : 0u;
+            } else {
+                // the raise becomes excess; the part the sink arc can take goes to t
+                const int m = min(e[j] + d, rt[j]);
+                const int en = e[j] + d - m;
+                if (ok && d) {
+                    const size_t idx = (size_t)y * pitch + T.X;
+                    __stcg(E + idx, en);
+                    if (m) __stcg(RT + idx, rt[j] - m);
+                }
+                sent += ok ? m : 0;
+                live |= (ok && en > 0 && h[j] < HINF) ? (1u << (c0 + j)) : 0u;
             }
-            sent += ok ? m : 0;
-            live |= (ok && en > 0 && h[j] < HINF) ? (1u << (c0 + j)) : 0u;
         }
     }
     int cnt[SPAN];
@@ -1317,9 +1344,11 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
 // --------------------------------------------------------------------------
 constexpr int WORKER_WARPS = 4;
 
-template <int TH, int PO>
+template <int TH, int PO, bool SINK>
 // at least 4 resident blocks per SM at tile height 4 (128 registers) and 2 at
-// height 8: with fewer, throughput-bound batches lose more than the spills cost
+// height 8: with fewer, throughput-bound batches lose more than the spills cost.
+// SINK: the batch holds instances whose sink capacities fall with lambda
+// (their own kernels, so that the others' register allocation is untouched)
 __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_kernel(const __grid_constant__ Params P) {
     __shared__ WarpSmem<TH> smem[WORKER_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1375,7 +1404,7 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_ker
             bfs_visit<TH, false>(P, S, g, inst, D, epoch, k, requeue, nb);
         else if (status == PMF_OK && phase == PH_FWD && !stray)
             bfs_visit<TH, true>(P, S, g, inst, D, epoch, k, requeue, nb);
-        else if (status == PMF_OK && phase == PH_WARM && !stray) warm_visit<TH>(P, g, inst, D, k);
+        else if (status == PMF_OK && phase == PH_WARM && !stray) warm_visit<TH, SINK>(P, g, inst, D, k);
         __threadfence();
         __syncwarp();
         if (prof) {
@@ -1538,12 +1567,18 @@ __global__ void init_kernel(const __grid_constant__ Params P) {
     int bad = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < PS; i += (size_t)gridDim.x * blockDim.x) {
         const int s0 = base[P_SRC0 * PS + i], sl = base[P_SLOPE * PS + i], ct = base[P_CT * PS + i];
-        const long long cs0 = (long long)s0 + (long long)sl * lam0;
-        const long long csN = (long long)s0 + (long long)sl * lamN;
-        if (cs0 < 0) bad |= VF_NEG;
+        // the source capacities rise with lambda, or the sink capacities fall
+        // (Section 2.1's monotone case either way): both stay within
+        // [0, PMF_INF] over the whole schedule
+        const long long up0 = D.slope_side ? 0 : (long long)sl * lam0, upN = D.slope_side ? 0 : (long long)sl * lamN;
+        const long long dn0 = D.slope_side ? (long long)sl * lam0 : 0, dnN = D.slope_side ? (long long)sl * lamN : 0;
+        const long long cs0 = (long long)s0 + up0, csN = (long long)s0 + upN;
+        const long long ct0 = (long long)ct - dn0, ctN = (long long)ct - dnN;
+        if (cs0 < 0 || ctN < 0) bad |= VF_NEG;
         if (csN > PMF_INF) bad |= VF_OVERFLOW;
-        int e = (cs0 < 0 || csN > PMF_INF) ? 0 : (int)cs0;
-        int rt = ct;
+        const bool ok = cs0 >= 0 && ctN >= 0 && csN <= PMF_INF;
+        int e = ok ? (int)cs0 : 0;
+        int rt = ok ? (int)ct0 : 0;
         const int m = min(e, rt);
         e -= m;
         rt -= m;
@@ -1639,7 +1674,7 @@ constexpr int RETURN_THREADS = 1024;
 // change: the value stays the flow into t.
 __global__ void __launch_bounds__(RETURN_THREADS) return_excess_kernel(
     const int32_t *E, const int32_t *RT, const int32_t *FR, const int32_t *FD, const int32_t *SRC0,
-    const int32_t *SLOPE, const int32_t *CT, int lambda, int H, int W, int pitch, int max_sweeps,
+    const int32_t *SLOPE, const int32_t *CT, int lambda, int slope_side, int H, int W, int pitch, int max_sweeps,
     int32_t *f_h, int32_t *f_v, int32_t *f_s, int32_t *f_t, int32_t *status) {
     const int n = H * W;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
@@ -1647,7 +1682,7 @@ __global__ void __launch_bounds__(RETURN_THREADS) return_excess_kernel(
         const size_t i = (size_t)y * pitch + x;
         f_h[p] = x < W - 1 ? FR[i] : 0;
         f_v[p] = y < H - 1 ? FD[i] : 0;
-        f_s[p] = SRC0[i] + SLOPE[i] * lambda;
+        f_s[p] = slope_side ? SRC0[i] : SRC0[i] + SLOPE[i] * lambda;
         f_t[p] = E[i];                      // the excess, until the last step
     }
     __syncthreads();
@@ -1694,7 +1729,7 @@ __global__ void __launch_bounds__(RETURN_THREADS) return_excess_kernel(
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
         const int y = p / W, x = p - y * W;
         const size_t i = (size_t)y * pitch + x;
-        f_t[p] = CT[i] - RT[i];
+        f_t[p] = (slope_side ? CT[i] - SLOPE[i] * lambda : CT[i]) - RT[i];
     }
     if (threadIdx.x == 0) *status = more ? 1 : 0;
 }
@@ -1707,7 +1742,7 @@ cudaError_t launch_return_excess(const Params &P, const DevInst &d, int lambda, 
     (void)cudaGetLastError();
     return_excess_kernel<<<1, RETURN_THREADS, 0, s>>>(base + P_E * PS, base + P_RT * PS, base + P_FR * PS,
                                                       base + P_FD * PS, base + P_SRC0 * PS, base + P_SLOPE * PS,
-                                                      base + P_CT * PS, lambda, d.H, d.W, d.pitch, max_sweeps,
+                                                      base + P_CT * PS, lambda, d.slope_side, d.H, d.W, d.pitch, max_sweeps,
                                                       f_h, f_v, f_s, f_t, status);
     return cudaGetLastError();
 }
@@ -1715,12 +1750,21 @@ cudaError_t launch_return_excess(const Params &P, const DevInst &d, int lambda, 
 cudaError_t launch_worker(const Params &P, int grid, cudaStream_t s) {
     (void)cudaGetLastError();
     // one kernel per tile height and push order: each holds only the sweep it runs
-    if (P.tile_h == 4) {
-        if (P.chain_push) worker_kernel<4, 1><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
-        else worker_kernel<4, 0><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
+    const dim3 b(WORKER_WARPS * 32);
+    if (P.any_sink_side) {
+        if (P.tile_h == 4) {
+            if (P.chain_push) worker_kernel<4, 1, true><<<grid, b, 0, s>>>(P);
+            else worker_kernel<4, 0, true><<<grid, b, 0, s>>>(P);
+        } else {
+            if (P.chain_push) worker_kernel<8, 1, true><<<grid, b, 0, s>>>(P);
+            else worker_kernel<8, 0, true><<<grid, b, 0, s>>>(P);
+        }
+    } else if (P.tile_h == 4) {
+        if (P.chain_push) worker_kernel<4, 1, false><<<grid, b, 0, s>>>(P);
+        else worker_kernel<4, 0, false><<<grid, b, 0, s>>>(P);
     } else {
-        if (P.chain_push) worker_kernel<8, 1><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
-        else worker_kernel<8, 0><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
+        if (P.chain_push) worker_kernel<8, 1, false><<<grid, b, 0, s>>>(P);
+        else worker_kernel<8, 0, false><<<grid, b, 0, s>>>(P);
     }
     return cudaGetLastError();
 }
@@ -1735,8 +1779,8 @@ int worker_warps_per_block() { return WORKER_WARPS; }
 
 cudaError_t worker_occupancy(int tile_h, int *blocks_per_sm) {
     if (tile_h == 4)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<4, 0>, WORKER_WARPS * 32, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<8, 0>, WORKER_WARPS * 32, 0);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<4, 0, false>, WORKER_WARPS * 32, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<8, 0, false>, WORKER_WARPS * 32, 0);
 }
 
 }  // namespace pmf

@@ -39,7 +39,8 @@ EXPORTS = ["pmf_workspace_size", "pmf_create_batch", "pmf_set_tuning", "pmf_get_
            "pmf_get_cut", "pmf_get_flow", "pmf_get_cuts", "pmf_get_flows", "pmf_get_timing",
            "pmf_get_stats", "pmf_get_trace", "pmf_get_profile", "pmf_get_mask_layout",
            "pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error",
-           "pmf_solve_noalloc", "pmf_get_flow_arcs", "pmf_set_cut_rule"]
+           "pmf_solve_noalloc", "pmf_get_flow_arcs", "pmf_set_cut_rule",
+           "pmf_set_slope_side"]
 
 
 class PmfError(RuntimeError):
@@ -123,6 +124,7 @@ def lib(path: str | None = None):
             L.pmf_get_flows.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64)]
             L.pmf_get_flow_arcs.argtypes = [vp, i32, vp, vp, vp, vp]
             L.pmf_set_cut_rule.argtypes = [vp, i32, i32]
+            L.pmf_set_slope_side.argtypes = [vp, i32, i32]
             L.pmf_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
             L.pmf_get_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
             L.pmf_get_trace.argtypes = [vp, ctypes.POINTER(TraceEvent), i32, i32p]
@@ -341,6 +343,11 @@ class Batch:
         """rule 1: the instance's terminals were passed with s and t swapped
         (see pmf_set_cut_rule); cuts then come back for the original problem."""
         _check(lib().pmf_set_cut_rule(self._h, int(inst), int(rule)), "pmf_set_cut_rule")
+
+    def set_slope_side(self, inst: int, side: int) -> None:
+        """0: source capacities src0 + slope*lambda rise with lambda (default);
+        1: sink capacities sink - slope*lambda fall (see pmf_set_slope_side)."""
+        _check(lib().pmf_set_slope_side(self._h, int(inst), int(side)), "pmf_set_slope_side")
 
     def flow_arcs(self, inst: int) -> dict:
         """A feasible maximum flow of the instance at its last lambda, per arc:

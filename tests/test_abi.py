@@ -79,5 +79,7 @@ def test_null_arguments_are_rejected_without_gpu():
     assert L.pmf_get_flow(None, 0, 0, None) == pmf.PMF_ERR_INVALID_ARG
     assert L.pmf_get_flow_arcs(None, 0, None, None, None, None) == pmf.PMF_ERR_INVALID_ARG
     assert L.pmf_copy_terminals(None, 0, 0) == pmf.PMF_ERR_INVALID_ARG
+    assert L.pmf_set_cut_rule(None, 0, 1) == pmf.PMF_ERR_INVALID_ARG
+    assert L.pmf_set_slope_side(None, 0, 1) == pmf.PMF_ERR_INVALID_ARG
     assert L.pmf_solve_schedules(None, None, None, 1, None) == pmf.PMF_ERR_INVALID_ARG
     L.pmf_destroy_batch(None)

@@ -29,6 +29,54 @@ def test_rule_counts_strictly():
     assert (d < 0).sum() == 0 and not swap.needs_swap(src0, slope, sink, 5)
 
 
+@pytest.mark.parametrize("shape,seed", [((1, 1), 0), ((3, 4), 1), ((4, 4), 2), ((2, 7), 3), ((6, 9), 4),
+                                        ((12, 15), 5)])
+def test_warm_swapped_schedule_reproduces_every_lambda(shape, seed):
+    """The exchanged chain at mu_j = lambda_last - lambda_{m-1-j}, with source
+    capacities ct and sink capacities sink' - slope*mu_j, is the original
+    problem at lambda_{m-1-j} with s and t exchanged: same flow value, and the
+    complement of its minimal source set is the original maximal source set."""
+    H, W = shape
+    rng = np.random.default_rng(1300 + seed)
+    wl = inputs.random_grid(H, W, rng, p_zero=0.3, n_lambda=min(5, H * W + 1), lam_max=25)
+    im, inst = wl.images[0], wl.instances[0]
+    a, b, c, mu = swap.warm_swapped_terminals(inst.src0, inst.slope, inst.sink, inst.lambdas)
+    m = len(inst.lambdas)
+    assert np.all(np.diff(mu) >= 0) and mu[0] == 0
+    assert np.array_equal(a, inst.sink) and np.array_equal(b, inst.slope)
+    f, masks = oracle.grid_solve(H, W, im.w_h, im.w_v, inst.src0, inst.slope, inst.sink, inst.lambdas)
+    N = H * W
+    zero = np.zeros_like(a)
+    for j in range(m):
+        ct_mu = (np.asarray(c, np.int64) - np.asarray(b, np.int64) * int(mu[j])).astype(np.int32)
+        assert ct_mu.min() >= 0
+        tail, head, cap = oracle.grid_arcs(H, W, im.w_h, im.w_v, a, zero, ct_mu, 0)
+        val, fl, _ = oracle.maxflow(N + 2, tail, head, cap, N, N + 1)
+        assert val == int(f[m - 1 - j])
+        minsrc = oracle.source_reach(N + 2, tail, head, cap, fl, N)[:N].reshape(H, W)
+        assert np.array_equal(1 - minsrc, masks[m - 1 - j])
+
+
+def test_warm_swapped_terminals_checks_its_inputs():
+    z = np.zeros(4, np.int32)
+    with pytest.raises(ValueError):
+        swap.warm_swapped_terminals(z, z, z, [3, 2])
+    with pytest.raises(ValueError):
+        swap.warm_swapped_terminals(z, z, z, [])
+    with pytest.raises(ValueError):
+        swap.warm_swapped_terminals(np.full(4, 1 << 29, np.int32), np.full(4, 1 << 20, np.int32), z, [0, 1024])
+
+
+def test_chain_rule_is_a_majority_of_the_lambdas():
+    src0 = np.zeros(4, np.int32)
+    slope = np.ones(4, np.int32)
+    sink = np.array([5, 5, 5, 1], np.int32)
+    # lambda 2 and 3 vote swap, 5 and 6 do not: a tie keeps the chain as it is
+    assert not swap.chain_needs_swap(src0, slope, sink, [2, 3, 5, 6])
+    assert swap.chain_needs_swap(src0, slope, sink, [2, 3, 5])
+    assert not swap.chain_needs_swap(src0, slope, sink, [2, 5, 6])
+
+
 @pytest.fixture(scope="module")
 def gpu():
     import torch
@@ -39,8 +87,8 @@ def gpu():
     return True
 
 
-def _check(wl, mode):
-    st, res, sw = swap.solve_workload(wl, swap=mode)
+def _check(wl, mode, warm=False, **tuning):
+    st, res, sw = swap.solve_workload(wl, swap=mode, warm=warm, **tuning)
     ref = oracle.solve_workload(wl)
     for i, ((f, m), (of, om)) in enumerate(zip(res, ref)):
         assert all(s == 0 for s in st[i]), st[i]
@@ -91,3 +139,39 @@ def test_cut_rule_on_a_multi_lambda_constant_problem(gpu):
     assert np.all(flows == f[0])
     for k in range(3):
         assert np.array_equal(cuts[k], m[0])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", [(1, 1), (1, 9), (9, 1), (7, 33), (16, 31), (33, 97), (40, 70)])
+@pytest.mark.parametrize("mode", ["always", "auto"])
+def test_warm_swapped_chains_random_grids(gpu, shape, mode):
+    """Warm-started chains, swapped as a whole: the exchanged problem runs the
+    schedule backwards with falling sink capacities, and every step's flow and
+    mask must equal the oracle's for the original problem at that lambda."""
+    H, W = shape
+    rng = np.random.default_rng(57 * H + W)
+    wl = inputs.random_grid(H, W, rng, wmax=20, tmax=40, p_zero=0.2, n_lambda=min(6, 31), lam_max=30)
+    sw = _check(wl, mode, warm=True)
+    if mode == "always":
+        assert all(all(x) for x in sw)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("push_order", [0, 1])
+def test_warm_swapped_chains_segmentation(gpu, push_order):
+    """Synthetic segmentation chains over 8 lambdas, every seed swapped, with
+    both push orders: parity with the oracle at every lambda."""
+    wl = inputs.parametric_320x240(n_lambda=8)
+    _check(wl, "always", warm=True, push_order=push_order)
+
+
+@pytest.mark.gpu
+def test_warm_swapped_and_plain_chains_in_one_batch(gpu):
+    """Seeds of the supergraph workload (5 of them, 6 lambdas), each chain
+    swapped or not by the rule; swapped and plain chains share one launch."""
+    wl = inputs.supergraph_480x320()
+    wl.instances = [inputs.Instance(x.image, x.src0, x.slope, x.sink, x.lambdas[::4].copy())
+                    for x in wl.instances[::5]]
+    sw = _check(wl, "auto", warm=True)
+    _check(wl, "always", warm=True)
+    assert len(sw) == 5
