@@ -186,8 +186,10 @@ PMF_API pmf_status pmf_set_terminals(pmf_batch *b, int32_t inst, const int32_t *
  * device-to-device copy queued on the batch's stream, no host transfer.  For
  * one problem split into several instances, e.g. a seed's schedule cut into
  * pieces that run side by side (Section 3.1's supergraph of (seed, lambda)
- * problems).  PMF_ERR_INVALID_ARG for an index out of range or instances of
- * different images; dst == src does nothing. */
+ * problems).  Only the capacity planes are copied: dst keeps its own cut rule
+ * and slope side (pmf_set_cut_rule, pmf_set_slope_side).  PMF_ERR_INVALID_ARG
+ * for an index out of range or instances of different images; dst == src does
+ * nothing. */
 PMF_API pmf_status pmf_copy_terminals(pmf_batch *b, int32_t dst, int32_t src);
 
 /* Section 3.2's s-t swap: the caller may solve an instance with s and t
