@@ -202,6 +202,7 @@ def run_ours(args, rank, world, dev):
     m = min(len(i.lambdas) for i in wl.instances)
     segments, tuning, mode_probe = resolve_mode(args, wl, dev, tuning0)
     args.mode = mode_name(segments, m)
+    wl_whole = wl
     if segments > 1:
         wl = wl.split_segments(segments)
     stream = torch.cuda.Stream(device=dev)
@@ -295,6 +296,9 @@ def run_ours(args, rank, world, dev):
     if not args.no_e2e:
         out["e2e"] = e2e(args, wl, b, lam, dev, stream, pmf, world)
     b.close()
+    if rank == 0 and not args.no_other_mode and min(len(i.lambdas) for i in wl_whole.instances) > 1:
+        out["other_mode"] = other_mode(args, wl_whole, segments, tuning, dev, flush, pmf)
+        out["other_mode"]["headline_over_other"] = value / world / out["other_mode"]["value"]
     if rank == 0 and args.serving_requests > 0:
         out["serving"] = serving_bench(args, dev)
     if rank == 0 and not args.no_cpu_baseline:
@@ -363,6 +367,60 @@ def per_solve_launch(args, wl, dev, pmf):
     return {"value": pix / t, "unit": UNIT, "solves": int(len(pick)),
             "sample": f"{len(pick)} random (seed, lambda) solves of the workload, each its own batch, "
                       "cold start, one worker launch per round with a host poll in between"}
+
+
+# knobs of the lambda-concurrent mode when the autotuner has no entry for it:
+# the faster of the two settings measured on the supergraph workload
+M1_KNOBS = {"tile_h": 4, "push_order": 1, "sweeps": 8, "relabel_every": 800, "label_slack": 16}
+
+
+def other_mode(args, wl, segments, tuning, dev, flush, pmf):
+    """The batching mode the headline did not use, timed the same way (L2
+    flushed, CUDA events on the solve's stream, a few steps): lambda-concurrent
+    (every (seed, lambda) its own cold instance) beside a warm-started
+    headline, else one warm-started chain per seed."""
+    import torch
+    from paper_1509_06004_b300 import autotune
+    m = min(len(i.lambdas) for i in wl.instances)
+    other = 1 if segments == m else m
+    wl2 = wl.split_segments(other) if other > 1 else wl
+    c = autotune.cached(wl2, dev.index)
+    if c is not None:
+        knobs = {k: c.get(k, v) for k, v in autotune.DEFAULTS.items()}
+        src = "autotune cache"
+    elif other == m:
+        knobs = dict(autotune.DEFAULTS, **M1_KNOBS)
+        src = "fixed (no autotune entry)"
+    else:
+        knobs = dict(tuning)
+        src = "the headline's knobs"
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        b = pmf.batch_from_workload(wl2, device=dev.index, stream=stream, **knobs)
+    lam = np.stack([i.lambdas for i in wl2.instances]).astype(np.int32)
+    steps = max(1, min(args.steps, 5))
+    for _ in range(3):
+        b.solve(lam, stream=stream)
+        b.sync()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize(dev)
+    for s in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(s)
+        ev0[s].record(stream)
+        b.solve(lam, stream=stream)
+        ev1[s].record(stream)
+        st = b.sync(check=False)
+        if any(x != pmf.PMF_OK for x in st):
+            raise RuntimeError("solve failed in the other mode")
+    torch.cuda.synchronize(dev)
+    b.close()
+    ms = float(np.mean([a.elapsed_time(z) for a, z in zip(ev0, ev1)]))
+    return {"mode": mode_name(other, m), "description": MODE_TEXT.get(mode_name(other, m), mode_name(other, m)),
+            "value": wl2.pixel_solves / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "knobs": {k: knobs[k] for k in ("tile_h", "push_order", "sweeps", "relabel_every", "label_slack")
+                      if k in knobs}, "knobs_source": src}
 
 
 def e2e(args, wl, b, lam, dev, stream, pmf, world):
@@ -523,6 +581,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-per-solve", action="store_true")
+    ap.add_argument("--no-other-mode", action="store_true",
+                    help="skip timing the batching mode the headline did not use")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=40, help="0 = skip the serving run")
     ap.add_argument("--serving-rate", type=float, default=50.0)
