@@ -138,3 +138,66 @@ def test_flow_arcs_with_falling_sink_capacities(P, shape):
     f, _ = oracle_falling(im, inst)
     assert val == int(f[-1]) == int(b.flows(0)[-1])
     b.close()
+
+
+@pytest.mark.parametrize("case", range(30))
+def test_fuzz_mixed_sides_and_swapped_chains(P, case):
+    """Random shapes, schedules and knobs; one batch mixes rising-source
+    instances, falling-sink instances and swapped warm-started chains (side 1
+    with cut rule 1, schedule run backwards); solved twice."""
+    from paper_1509_06004_b300 import swap
+    rng = np.random.default_rng(9000 + case)
+    H, W = int(rng.integers(1, 65)), int(rng.integers(1, 97))
+    n_lam = int(rng.integers(1, 7))
+    base = inputs.random_grid(H, W, rng, wmax=int(rng.integers(1, 40)), tmax=40, p_zero=float(rng.uniform(0, 0.5)),
+                              n_lambda=n_lam, lam_max=40)
+    im = base.images[0]
+    insts, kinds = [], []
+    for _ in range(int(rng.integers(1, 5))):
+        g = inputs.random_grid(H, W, rng, tmax=int(rng.integers(1, 60)), p_zero=float(rng.uniform(0, 0.5)),
+                               n_lambda=n_lam, lam_max=40).instances[0]
+        kind = int(rng.integers(0, 3))          # 0 rising source, 1 falling sink, 2 swapped chain
+        if kind == 1:
+            g = falling_instance_from(g)
+        insts.append(g)
+        kinds.append(kind)
+    refs = []
+    for g, kind in zip(insts, kinds):
+        if kind == 1:
+            refs.append(oracle_falling(im, g))
+        else:
+            refs.append(oracle.grid_solve(H, W, im.w_h, im.w_v, g.src0, g.slope, g.sink, g.lambdas))
+    flat = inputs.Workload("fuzz", base.images, [])
+    for g, kind in zip(insts, kinds):
+        if kind == 2:
+            a, b_, c, mu = swap.warm_swapped_terminals(g.src0, g.slope, g.sink, g.lambdas)
+            flat.instances.append(inputs.Instance(0, a, b_, c, mu))
+        else:
+            flat.instances.append(g)
+    knobs = dict(tile_h=int(rng.choice([4, 8])), push_order=int(rng.integers(0, 2)),
+                 sweeps=int(rng.choice([1, 2, 4, 8, 16])), relabel_every=int(rng.choice([50, 200, 800, 1600])),
+                 label_slack=int(rng.choice([0, 2, 4, 16])))
+    b = P.batch_from_workload(flat, **knobs)
+    for j, kind in enumerate(kinds):
+        if kind:
+            b.set_slope_side(j, 1)
+        if kind == 2:
+            b.set_cut_rule(j, 1)
+    for _ in range(2):
+        b.solve(np.stack([x.lambdas for x in flat.instances]).astype(np.int32))
+        st = b.sync(check=False)
+        for j, (kind, (rf, rm)) in enumerate(zip(kinds, refs)):
+            assert st[j] == P.PMF_OK, (j, kind, st[j])
+            f, m = b.flows(j), b.cuts(j)
+            if kind == 2:
+                f, m = f[::-1], m[::-1]
+            assert np.array_equal(f, rf), (j, kind, knobs, f, rf)
+            assert np.array_equal(m, rm), (j, kind, knobs)
+    b.close()
+
+
+def falling_instance_from(inst):
+    """The same instance with sink capacities that fall to its own at the last lambda."""
+    lam_last = int(inst.lambdas[-1])
+    sink = (inst.sink.astype(np.int64) + inst.slope.astype(np.int64) * lam_last).astype(np.int32)
+    return inputs.Instance(inst.image, inst.src0, inst.slope, sink, inst.lambdas)
