@@ -44,6 +44,7 @@ L2_FLUSH_BYTES = 512 << 20
 WORKLOADS = {
     "supergraph-480x320": lambda seed: inputs.supergraph_480x320(seed=seed),
     "supergraph-480x320-5seeds": lambda seed: _first_instances(inputs.supergraph_480x320(seed=seed), 5),
+    "supergraph-480x320-15seeds": lambda seed: _first_instances(inputs.supergraph_480x320(seed=seed), 15),
     "parametric-320x240": lambda seed: inputs.parametric_320x240(seed=seed),
     "uneven-64": lambda seed: inputs.uneven_batch(first_seed=64 * seed),
     "single-64x64": lambda seed: inputs.single_maxflow_64(seed=seed),
