@@ -466,3 +466,37 @@ def test_swap_keeps_value_and_complements_the_minimal_source_set(shape, seed):
         if N <= 16:
             bf = oracle.brute_force_min_source_set(N + 2, tail, head, cap, N, N + 1)[:N].reshape(H, W)
             assert np.array_equal(bf, minsrc)
+
+
+# --------------------------------------------------------------------------
+# the other half of Section 2.1's monotone case: sink capacities that fall
+# with lambda (ct = sink - slope*lambda, cs = src0).  F is then a minimum of
+# affine functions with non-positive slopes: nonincreasing and concave; the
+# maximal source sets still grow with lambda
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,seed", [((1, 1), 0), ((2, 3), 1), ((3, 4), 2), ((4, 4), 3), ((6, 9), 4),
+                                        ((12, 15), 5)])
+def test_falling_sink_capacities_nested_and_concave(shape, seed):
+    H, W = shape
+    rng = np.random.default_rng(2100 + seed)
+    wl = inputs.random_grid(H, W, rng, p_zero=0.3, n_lambda=min(6, H * W + 3), lam_max=20)
+    im, inst = wl.images[0], wl.instances[0]
+    lams = [int(x) for x in inst.lambdas]
+    sink = inst.sink.astype(np.int64) + inst.slope.astype(np.int64) * lams[-1]
+    zero = np.zeros_like(inst.slope)
+    flows, masks = [], []
+    for lam in lams:
+        ct = (sink - inst.slope.astype(np.int64) * lam).astype(np.int32)
+        f, m = oracle.grid_solve(H, W, im.w_h, im.w_v, inst.src0, zero, ct, [0])
+        flows.append(int(f[0]))
+        masks.append(m[0])
+        if H * W <= 16:
+            cost, bm, _ = oracle.brute_force_grid(H, W, im.w_h, im.w_v, inst.src0, zero, ct, 0)
+            assert cost == int(f[0]) and np.array_equal(bm, m[0])
+    for k in range(len(lams) - 1):
+        assert np.all(masks[k] <= masks[k + 1])
+        assert flows[k + 1] <= flows[k]
+    for k in range(1, len(lams) - 1):
+        d0 = (flows[k] - flows[k - 1]) * (lams[k + 1] - lams[k])
+        d1 = (flows[k + 1] - flows[k]) * (lams[k] - lams[k - 1])
+        assert d1 <= d0
