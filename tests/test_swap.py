@@ -175,3 +175,59 @@ def test_warm_swapped_and_plain_chains_in_one_batch(gpu):
     sw = _check(wl, "auto", warm=True)
     _check(wl, "always", warm=True)
     assert len(sw) == 5
+
+
+def test_warm_chains_host_logic_with_a_fake_batch(monkeypatch):
+    """swap.solve_workload(warm=True) without a GPU: swapped chains are marked
+    with cut rule 1 and slope side 1, get the reversed mu schedule, and their
+    results come back reversed into the original lambda order; plain chains
+    pass through untouched."""
+    from paper_1509_06004_b300 import pmf
+    wl = inputs.random_grid(3, 5, np.random.default_rng(3), n_lambda=4, lam_max=20)
+    inst = wl.instances[0]
+    wl.instances.append(inputs.Instance(0, inst.src0, inst.slope, inst.sink, inst.lambdas))
+    calls = {}
+
+    class FakeBatch:
+        def __init__(self, flat):
+            self.flat = flat
+            calls["flat"] = flat
+            calls["rule"], calls["side"] = {}, {}
+
+        def set_cut_rule(self, j, r):
+            calls["rule"][j] = r
+
+        def set_slope_side(self, j, s):
+            calls["side"][j] = s
+
+        def solve(self, lam):
+            calls["lam"] = [np.asarray(x) for x in lam]
+
+        def sync(self, check=False):
+            return [pmf.PMF_OK] * len(self.flat.instances)
+
+        def flows(self, j):      # step k's "flow" is its own schedule value, to see the order
+            return np.asarray(self.flat.instances[j].lambdas, np.int64) * 10 + j
+
+        def cuts(self, j):
+            n = len(self.flat.instances[j].lambdas)
+            return np.stack([np.full((3, 5), k, np.uint8) for k in range(n)])
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(pmf, "batch_from_workload", lambda flat, device=0, **kw: FakeBatch(flat))
+    answers = iter([True, False])           # the rule swaps the first chain only
+    monkeypatch.setattr(swap, "chain_needs_swap", lambda *a: next(answers))
+    st, res, sw = swap.solve_workload(wl, swap="auto", warm=True)
+    lam = np.asarray(inst.lambdas, np.int64)
+    mu = lam[-1] - lam[::-1]
+    assert sw == [[True] * 4, [False] * 4]
+    assert calls["rule"] == {0: 1} and calls["side"] == {0: 1}
+    assert np.array_equal(calls["lam"][0], mu) and np.array_equal(calls["lam"][1], lam)
+    # swapped: result k belongs to lambda_k, i.e. to mu_{m-1-k}
+    assert np.array_equal(res[0][0], (mu * 10)[::-1])
+    assert [int(c[0, 0]) for c in res[0][1]] == [3, 2, 1, 0]
+    assert np.array_equal(res[1][0], lam * 10 + 1)
+    assert [int(c[0, 0]) for c in res[1][1]] == [0, 1, 2, 3]
+    assert st == [[pmf.PMF_OK] * 4, [pmf.PMF_OK] * 4]
