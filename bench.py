@@ -57,20 +57,39 @@ def _first_instances(wl, n):
     return wl
 
 
-def mode_name(segments: int, m: int) -> str:
-    return "m2" if segments == 1 else ("m1" if segments == m else f"seg{segments}")
-
-
 MODE_TEXT = {"m2": "lambda-sequential GGT warm start (one instance per seed)",
              "m1": "lambda-concurrent (one cold instance per seed x lambda)"}
 
 
+def mode_text(mode):
+    if mode in MODE_TEXT:
+        return MODE_TEXT[mode]
+    if mode.startswith("seg"):
+        return f"each seed's schedule in {mode[3:]} consecutive warm-started pieces"
+    if mode.startswith("ilv"):
+        return (f"each seed's schedule dealt round-robin into {mode[3:]} warm-started pieces "
+                "(piece j: lambda_j, lambda_j+P, ...)")
+    return mode
+
+
+def parse_mode(mode: str, m: int):
+    """Plan of an explicit --mode (m2, m1, seg<N>, ilv<N>); None for auto."""
+    if mode == "m2":
+        return {"segments": 1, "interleave": 1}
+    if mode == "m1":
+        return {"segments": m, "interleave": 1}
+    if mode.startswith("seg"):
+        return {"segments": int(mode[3:]), "interleave": 1}
+    if mode.startswith("ilv"):
+        return {"segments": 1, "interleave": int(mode[3:])}
+    return None
+
+
 def describe(wl, mode):
     ims = sorted({f"{wl.images[i.image].W}x{wl.images[i.image].H}" for i in wl.instances})
-    text = MODE_TEXT.get(mode, f"each seed's schedule in {mode[3:]} warm-started pieces" if mode.startswith("seg") else mode)
     return {"workload": wl.name, "images": len(wl.images), "image_sizes": ims,
             "instances": len(wl.instances), "lambdas_per_instance": int(len(wl.instances[0].lambdas)),
-            "solves": wl.n_solves, "pixel_solves": wl.pixel_solves, "mode": text}
+            "solves": wl.n_solves, "pixel_solves": wl.pixel_solves, "mode": mode_text(mode)}
 
 
 # ----------------------------------------------------------------------------
@@ -157,7 +176,7 @@ def quick_rate(wl, dev, tuning, reps=3):
     from paper_1509_06004_b300 import pmf
     stream = torch.cuda.Stream(device=dev)
     b = pmf.batch_from_workload(wl, device=dev.index, stream=stream, **tuning)
-    lam = np.stack([i.lambdas for i in wl.instances]).astype(np.int32)
+    lam = [np.asarray(i.lambdas, np.int32) for i in wl.instances]
     ts = []
     for _ in range(reps + 1):
         b.solve(lam, stream=stream)
@@ -168,27 +187,25 @@ def quick_rate(wl, dev, tuning, reps=3):
 
 
 def resolve_mode(args, wl, dev, tuning0):
-    """(segments, knobs, note) for the requested mode.  auto: the autotuner's
+    """(plan, knobs, note) for the requested mode.  auto: the autotuner's
     cached choice for this GPU and workload class, else the fastest of one
     chain per seed, the middle split and one instance per (seed, lambda)."""
     from paper_1509_06004_b300 import autotune
     m = min(len(i.lambdas) for i in wl.instances)
-    if args.mode == "m2":
-        return 1, tuning0, None
-    if args.mode == "m1":
-        return m, tuning0, None
-    if args.mode.startswith("seg"):
-        return int(args.mode[3:]), tuning0, None
+    plan = parse_mode(args.mode, m)
+    if plan is not None:
+        return plan, tuning0, None
     c = autotune.cached(wl, dev.index)
     if c is not None and not tuning0:
-        knobs = {k: c.get(k, v) for k, v in autotune.DEFAULTS.items()}
-        return int(c["segments"]), knobs, {"source": "autotune cache", "class": autotune.workload_class(wl),
-                                           "tuned_ms": c.get("ms")}
+        p = autotune.bench_plan(wl, dev.index)
+        return ({"segments": p["segments"], "interleave": p["interleave"]}, autotune.knobs_of(p),
+                {"source": "autotune cache", "class": autotune.workload_class(wl), "tuned_ms": c.get("ms")})
     divs = autotune.divisors(m)
     cands = sorted({1, divs[len(divs) // 2], m})
     probe = {s: quick_rate(wl.split_segments(s) if s > 1 else wl, dev, tuning0) for s in cands}
     best = min(probe, key=probe.get)
-    return best, tuning0, {"source": "probe", "ms": {mode_name(k, m): v for k, v in probe.items()}}
+    return ({"segments": best, "interleave": 1}, tuning0,
+            {"source": "probe", "ms": {autotune.plan_name({"segments": k}, m): v for k, v in probe.items()}})
 
 
 def run_ours(args, rank, world, dev):
@@ -200,16 +217,16 @@ def run_ours(args, rank, world, dev):
                                  ("relabel_every", args.relabel_every), ("label_slack", args.label_slack),
                                  ("push_order", args.push_order), ("relabel_extra", args.relabel_extra),
                                  ("poll_ns", args.poll_ns)) if v}
+    from paper_1509_06004_b300 import autotune
     m = min(len(i.lambdas) for i in wl.instances)
-    segments, tuning, mode_probe = resolve_mode(args, wl, dev, tuning0)
-    args.mode = mode_name(segments, m)
+    plan, tuning, mode_probe = resolve_mode(args, wl, dev, tuning0)
+    args.mode = autotune.plan_name(plan, m)
     wl_whole = wl
-    if segments > 1:
-        wl = wl.split_segments(segments)
+    wl = autotune.apply_plan(wl, plan)
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         b = pmf.batch_from_workload(wl, device=dev.index, stream=stream, **tuning)
-    lam = np.stack([i.lambdas for i in wl.instances]).astype(np.int32)
+    lam = autotune.schedules(wl)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     tile_px = 30 * b.tuning()["tile_h"]     # interior pixels of a tile
 
@@ -267,22 +284,36 @@ def run_ours(args, rank, world, dev):
     except (OSError, ValueError):
         pass
     peak = peaks.get("hbm_gbs", 6400.0)
-    traffic = _profiled_traffic(args, wl)
+    prof = _profiled(args, wl)
+    traffic = prof.get("traffic")
+    dram_gbs = traffic / (wk_ms / 1e3) / 1e9 if traffic else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": dict(describe(wl, args.mode), tile=f"30x{tile_px // 30} (+2 mirrored columns)",
+        "config": dict(describe(wl_whole, args.mode), tile=f"30x{tile_px // 30} (+2 mirrored columns)",
+                       instances_launched=len(wl.instances),
                        sweeps=b.tuning()["sweeps"], relabel_every_pct=b.tuning()["relabel_every"],
                        relabel_extra=b.tuning()["relabel_extra"], poll_ns=b.tuning()["poll_ns"],
                        label_slack=b.tuning()["label_slack"],
                        l2="flushed between timed steps (512 MB write)",
                        parallelism=f"replicas x{world} (independent instances, no collective)"),
         "solves_per_s": solves_s,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        # The worker is latency-bound (chains of dependent tile visits, each a
+        # few dependent global round trips): its DRAM traffic is a small part
+        # of the algorithmic bytes, which the visits re-read from L2.
+        # achieved/frac: algorithmic bytes per launch over the launch time,
+        # against the HBM copy peak; dram_gbs/dram_frac: the DRAM bytes ncu
+        # counted for the same kernel source and workload, over the same time.
+        "roofline": {"bound": "latency", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     "dram_gbs": dram_gbs, "dram_frac": dram_gbs / peak if dram_gbs else None,
+                     "issue_active": prof.get("issue_active"), "warps_active": prof.get("warps_active"),
+                     "bound_evidence": "ncu: DRAM far below peak, SM issue active a small fraction of "
+                                       "cycles, stalls on long_scoreboard and sleeping idle warps",
                      "kernel": "worker_kernel (persistent push/relabel + global relabel)",
                      "worker_ms": wk_ms, "alg_bytes_per_launch": alg_bytes,
+                     "achieved_is": "algorithmic bytes (mostly served by L2) / worker launch time",
                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                      "visits_per_launch": {"push_relabel_tiles": pr_v / args.steps, "bfs_strips": bfs_v / args.steps,
                                            "warm_start_strips": warm_v / args.steps}},
@@ -298,7 +329,7 @@ def run_ours(args, rank, world, dev):
         out["e2e"] = e2e(args, wl, b, lam, dev, stream, pmf, world)
     b.close()
     if rank == 0 and not args.no_other_mode and min(len(i.lambdas) for i in wl_whole.instances) > 1:
-        out["other_mode"] = other_mode(args, wl_whole, segments, tuning, dev, flush, pmf)
+        out["other_mode"] = other_mode(args, wl_whole, plan, tuning, dev, flush, pmf)
         out["other_mode"]["headline_over_other"] = value / world / out["other_mode"]["value"]
     if rank == 0 and args.serving_requests > 0:
         out["serving"] = serving_bench(args, dev)
@@ -317,21 +348,26 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic(args, wl):
-    """DRAM bytes per worker launch from the committed ncu summary
-    (profiles/worker_kernel_traffic.txt) when it was taken on the current
-    kernel source and matches this workload and mode; None otherwise."""
+def _profiled(args, wl):
+    """ncu figures of the worker kernel from the committed summary
+    (profiles/worker_kernel_traffic.txt), quoted only when they were taken on
+    the current kernel source: DRAM bytes per launch ("traffic") for this
+    workload and mode, and the issue-active and warps-active fractions."""
     p = os.path.join(ROOT, "profiles", "worker_kernel_traffic.txt")
     try:
         lines = [l.strip() for l in open(p) if l.strip() and not l.startswith("#")]
         cur = kernel_source_hash()
     except OSError:
-        return None
-    kv = dict(l.rsplit(":", 1) for l in lines)
+        return {}
+    kv = dict(l.rsplit(":", 1) for l in lines if ":" in l)
     if kv.get("kernel_sha256_16", "").strip() != cur:
-        return None
-    v = kv.get(f"{wl.name}|{args.mode}")
-    return float(v) if v is not None else None
+        return {}
+    out = {}
+    for key, name in ((f"{wl.name}|{args.mode}", "traffic"), (f"issue_active|{wl.name}|{args.mode}", "issue_active"),
+                      (f"warps_active|{wl.name}|{args.mode}", "warps_active")):
+        if key in kv:
+            out[name] = float(kv[key])
+    return out
 
 
 def per_solve_launch(args, wl, dev, pmf):
@@ -375,7 +411,7 @@ def per_solve_launch(args, wl, dev, pmf):
 M1_KNOBS = {"tile_h": 4, "push_order": 1, "sweeps": 8, "relabel_every": 800, "label_slack": 16}
 
 
-def other_mode(args, wl, segments, tuning, dev, flush, pmf):
+def other_mode(args, wl, plan, tuning, dev, flush, pmf):
     """The batching mode the headline did not use, timed the same way (L2
     flushed, CUDA events on the solve's stream, a few steps): lambda-concurrent
     (every (seed, lambda) its own cold instance) beside a warm-started
@@ -383,7 +419,7 @@ def other_mode(args, wl, segments, tuning, dev, flush, pmf):
     import torch
     from paper_1509_06004_b300 import autotune
     m = min(len(i.lambdas) for i in wl.instances)
-    other = 1 if segments == m else m
+    other = 1 if plan["segments"] == m else m
     wl2 = wl.split_segments(other) if other > 1 else wl
     c = autotune.cached(wl2, dev.index)
     if c is not None:
@@ -398,7 +434,7 @@ def other_mode(args, wl, segments, tuning, dev, flush, pmf):
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         b = pmf.batch_from_workload(wl2, device=dev.index, stream=stream, **knobs)
-    lam = np.stack([i.lambdas for i in wl2.instances]).astype(np.int32)
+    lam = autotune.schedules(wl2)
     steps = max(1, min(args.steps, 5))
     for _ in range(3):
         b.solve(lam, stream=stream)
@@ -418,7 +454,8 @@ def other_mode(args, wl, segments, tuning, dev, flush, pmf):
     torch.cuda.synchronize(dev)
     b.close()
     ms = float(np.mean([a.elapsed_time(z) for a, z in zip(ev0, ev1)]))
-    return {"mode": mode_name(other, m), "description": MODE_TEXT.get(mode_name(other, m), mode_name(other, m)),
+    name = autotune.plan_name({"segments": other}, m)
+    return {"mode": name, "description": mode_text(name),
             "value": wl2.pixel_solves / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "knobs": {k: knobs[k] for k in ("tile_h", "push_order", "sweeps", "relabel_every", "label_slack")
                       if k in knobs}, "knobs_source": src}
@@ -446,9 +483,10 @@ def e2e(args, wl, b, lam, dev, stream, pmf, world):
     for inst in wl.instances:
         im = wl.images[inst.image]
         outs.append(torch.empty((len(inst.lambdas), im.H, im.W), dtype=torch.uint8).pin_memory().numpy())
-    flows = np.empty((len(wl.instances), lam.shape[1]), np.int64)
-    h2d = sum(a.nbytes + c.nbytes for a, c in imgs) + sum(x.nbytes for t in terms if t for x in t) + lam.nbytes
-    d2h = sum(o.nbytes for o in outs) + flows.nbytes
+    flows = [np.empty(len(x), np.int64) for x in lam]
+    h2d = (sum(a.nbytes + c.nbytes for a, c in imgs) + sum(x.nbytes for t in terms if t for x in t)
+           + sum(x.nbytes for x in lam))
+    d2h = sum(o.nbytes for o in outs) + sum(f.nbytes for f in flows)
 
     def one():
         for i, (a, c) in enumerate(imgs):
@@ -569,7 +607,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="supergraph-480x320")
-    ap.add_argument("--mode", default="auto", help="auto | m2 | m1 | seg<N>")
+    ap.add_argument("--mode", default="auto", help="auto | m2 | m1 | seg<N> | ilv<N>")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tile-h", type=int, default=0)
     ap.add_argument("--sweeps", type=int, default=0)

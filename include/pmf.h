@@ -366,7 +366,11 @@ PMF_API const char *pmf_status_string(pmf_status s);
  * Errors: sizes beyond PMF_NOALLOC_MAX_PIXELS or PMF_NOALLOC_MAX_LAMBDAS give
  * PMF_ERR_OUT_OF_MEMORY before any GPU work; a decreasing schedule gives
  * PMF_ERR_NOT_MONOTONE; invalid capacities give the statuses pmf_sync reports
- * for a batch.
+ * for a batch; a failed CUDA call gives PMF_ERR_CUDA (pmf_last_error names
+ * it) after the call has waited for whatever GPU work it had queued.  The
+ * solver knobs are fixed: those the autotuner picks for one-instance
+ * workloads (tile height 4, pushes along columns and rows, 8 sweeps per
+ * visit, relabel cadence 800 %, label slack 16).
  *
  * The first call on a device looks up the array's device address for that
  * device (cudaGetSymbolAddress); make that first call before any stream
@@ -379,6 +383,15 @@ PMF_API pmf_status pmf_solve_noalloc(int32_t H, int32_t W, const int32_t *w_h, c
                                      const int32_t *src0, const int32_t *slope, const int32_t *sink,
                                      const int32_t *lambdas, int32_t n_lambda, uint8_t *masks,
                                      int64_t *flows, void *cuda_stream);
+
+/* Test hook for the error paths of pmf_solve_noalloc (no counterpart in the
+ * paper).  The n-th CUDA runtime call (counting from 1) of the NEXT
+ * pmf_solve_noalloc call reports a failure instead of being made, so that a
+ * test can check, without any GPU fault, that the call returns
+ * PMF_ERR_CUDA, names the site in pmf_last_error, and has waited for the GPU
+ * work it had already queued before releasing its lock (a later call then
+ * gives correct results).  n <= 0 clears it; it applies to one call only. */
+PMF_API void pmf_testing_fail_noalloc_call(int32_t n);
 
 /* Text of the last CUDA failure seen by this thread ("" if none): the call
  * site and cudaGetErrorString, for diagnostics after PMF_ERR_CUDA. */

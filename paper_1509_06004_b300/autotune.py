@@ -9,6 +9,9 @@ instance count and schedule length:
   per seed; schedule length = every (seed, lambda) cold, the paper's
   lambda-supergraph); more pieces give the GPU more independent work, fewer
   keep more warm-start reuse;
+* ``interleave`` — each seed's schedule is dealt round-robin into this many
+  pieces (piece j: lambda_j, lambda_{j+P}, ...): every piece starts cold at one
+  of the smallest lambdas and neighbouring lambdas of a seed run side by side;
 * ``tile_h`` (rows per tile), ``push_order`` (pushes from the sweep's starting
   state, or along columns and rows), ``sweeps`` (push/relabel sweeps per tile visit),
   ``relabel_every`` (visit budget of a push/relabel phase, percent of its
@@ -43,6 +46,53 @@ SPACE = {
     "relabel_extra": [0, 64, 256, 1024],
     "poll_ns": [256, 1024, 4096],
 }
+
+
+def apply_plan(wl, plan: dict):
+    """The workload as a plan batches it: each seed's schedule dealt into
+    ``plan["interleave"]`` round-robin pieces, then each piece cut into
+    ``plan["segments"]`` consecutive ones (both default to 1).  Every piece
+    records which lambdas of which seed it holds (``Workload.gather``)."""
+    w = wl
+    il = int(plan.get("interleave", 1) or 1)
+    if il > 1:
+        w = w.split_interleaved(il)
+    seg = int(plan.get("segments", 1) or 1)
+    if seg > 1:
+        w = w.split_segments(seg)
+    return w
+
+
+def schedules(wl) -> list:
+    """Per-instance lambda schedules of a workload (they may differ in length)."""
+    return [np.asarray(i.lambdas, np.int32) for i in wl.instances]
+
+
+def plan_name(plan: dict, m: int) -> str:
+    """Short name of a batching plan for a schedule of m lambdas: m2 (one
+    warm chain per seed), m1 (every (seed, lambda) cold), segN, ilvN."""
+    seg, il = int(plan.get("segments", 1) or 1), int(plan.get("interleave", 1) or 1)
+    if il > 1:
+        return f"ilv{il}" + (f"-seg{seg}" if seg > 1 else "")
+    return "m2" if seg == 1 else ("m1" if seg == m else f"seg{seg}")
+
+
+def bench_plan(wl, device: int = 0) -> dict:
+    """The plan and knobs the benchmark runs a workload with: the autotuner's
+    cached choice for this GPU and workload class, else the defaults with one
+    warm chain per seed."""
+    c = cached(wl, device)
+    out = {"segments": 1, "interleave": 1, **DEFAULTS}
+    if c is not None:
+        for k in out:
+            if k in c:
+                out[k] = c[k]
+    return out
+
+
+def knobs_of(plan: dict) -> dict:
+    """The solver knobs of a plan (pmf_set_tuning fields)."""
+    return {k: plan[k] for k in DEFAULTS if k in plan}
 
 
 def divisors(m: int) -> list[int]:
@@ -86,15 +136,17 @@ def cached(wl, device: int = 0, path: str = CACHE_PATH) -> dict | None:
     return load_cache(path).get(f"{gpu_name(device)}|{workload_class(wl)}")
 
 
-def gpu_measure(wl, segments: int, knobs: dict, reps: int = 3, device: int = 0) -> float:
+def gpu_measure(wl, segments, knobs: dict, reps: int = 3, device: int = 0) -> float:
     """Median device time (ms) of ``reps`` solves (after one warm-up) of the
-    workload cut into ``segments`` pieces per seed."""
+    workload cut into ``segments`` pieces per seed (an int), or batched by a
+    plan ({"segments", "interleave"})."""
     import torch
     from . import pmf
-    w = wl.split_segments(segments) if segments > 1 else wl
+    plan = segments if isinstance(segments, dict) else {"segments": segments}
+    w = apply_plan(wl, plan)
     stream = torch.cuda.Stream(device=device)
     b = pmf.batch_from_workload(w, device=device, stream=stream, **knobs)
-    lam = np.stack([i.lambdas for i in w.instances]).astype(np.int32)
+    lam = schedules(w)
     ts = []
     try:
         for r in range(reps + 1):
@@ -109,51 +161,63 @@ def gpu_measure(wl, segments: int, knobs: dict, reps: int = 3, device: int = 0) 
     return float(np.median(ts))
 
 
+INTERLEAVE = [2, 3, 4, 5, 6, 8, 10]
+
+
+def plans_for(m: int) -> list[dict]:
+    """Batching plans tried for a schedule of m lambdas: consecutive pieces
+    (every divisor of m) and round-robin pieces (a few strides)."""
+    out = [{"segments": d, "interleave": 1} for d in divisors(m)]
+    out += [{"segments": 1, "interleave": p} for p in INTERLEAVE if p < m]
+    return out
+
+
 def tune(wl, measure=None, budget_s: float = 90.0, reps: int = 3, log=None) -> dict:
-    """Coordinate descent over ``segments`` then each knob of SPACE, starting
-    from DEFAULTS; stops when a full pass brings no gain or the time budget is
-    spent.  ``measure(wl, segments, knobs) -> ms`` defaults to gpu_measure.
-    Returns {"segments", knobs..., "ms"}."""
-    measure = measure or (lambda w, s, k: gpu_measure(w, s, k, reps=reps))
+    """Coordinate descent over the batching plan (``segments`` /
+    ``interleave``) then each knob of SPACE, starting from one warm chain per
+    seed and DEFAULTS; stops when a full pass brings no gain or the time
+    budget is spent.  ``measure(wl, plan, knobs) -> ms`` defaults to
+    gpu_measure.  Returns {"segments", "interleave", knobs..., "ms"}."""
+    measure = measure or (lambda w, p, k: gpu_measure(w, p, k, reps=reps))
     m = min(len(i.lambdas) for i in wl.instances)
-    segs = [d for d in divisors(m)]
+    plans = plans_for(m)
     t_end = time.monotonic() + budget_s
     seen: dict = {}
 
-    def cost(s, k):
-        key = (s, tuple(sorted(k.items())))
+    def cost(p, k):
+        key = (tuple(sorted(p.items())), tuple(sorted(k.items())))
         if key not in seen:
-            seen[key] = measure(wl, s, dict(k))
+            seen[key] = measure(wl, dict(p), dict(k))
             if log:
-                log(f"segments={s} {k} -> {seen[key]:.2f} ms")
+                log(f"plan={plan_name(p, m)} {k} -> {seen[key]:.2f} ms")
         return seen[key]
 
-    best_s, best_k = 1, dict(DEFAULTS)
-    best = cost(best_s, best_k)
+    best_p, best_k = plans[0], dict(DEFAULTS)
+    best = cost(best_p, best_k)
     improved = True
     while improved and time.monotonic() < t_end:
         improved = False
-        for s in segs:
+        for p in plans:
             if time.monotonic() >= t_end:
                 break
-            c = cost(s, best_k)
+            c = cost(p, best_k)
             if c < best:
-                best, best_s, improved = c, s, True
+                best, best_p, improved = c, p, True
         for name, vals in SPACE.items():
             for v in vals:
                 if time.monotonic() >= t_end:
                     break
                 k = dict(best_k)
                 k[name] = v
-                c = cost(best_s, k)
+                c = cost(best_p, k)
                 if c < best:
                     best, best_k, improved = c, k, True
-    out = {"segments": best_s, **best_k, "ms": best}
+    out = {**best_p, **best_k, "ms": best}
     return out
 
 
 def tune_and_cache(wl, device: int = 0, budget_s: float = 90.0, path: str = CACHE_PATH, log=None) -> dict:
-    res = tune(wl, measure=lambda w, s, k: gpu_measure(w, s, k, reps=3, device=device), budget_s=budget_s, log=log)
+    res = tune(wl, measure=lambda w, p, k: gpu_measure(w, p, k, reps=3, device=device), budget_s=budget_s, log=log)
     cache = load_cache(path)
     res["class"] = workload_class(wl)
     cache[f"{gpu_name(device)}|{workload_class(wl)}"] = res

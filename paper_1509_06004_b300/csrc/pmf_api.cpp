@@ -215,7 +215,7 @@ struct pmf_batch {
     int worker_grid = 0;
 };
 
-namespace {
+namespace pmf {
 
 thread_local char g_last_error[256] = "";
 
@@ -224,6 +224,11 @@ pmf_status cuda_err_at(cudaError_t e, const char *where) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
     return PMF_ERR_CUDA;
 }
+
+}  // namespace pmf
+
+namespace {
+
 #define cuda_err(e) cuda_err_at((e), __func__)
 
 void apply_defaults(pmf_tuning *t) {

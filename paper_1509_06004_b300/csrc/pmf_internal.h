@@ -159,6 +159,9 @@ cudaError_t launch_return_excess(const Params &P, const DevInst &d, int lambda, 
                                  int32_t *f_h, int32_t *f_v, int32_t *f_s, int32_t *f_t, int32_t *status,
                                  cudaStream_t s);
 int worker_warps_per_block();
+// records "where: <CUDA error text>" for pmf_last_error (this thread) and
+// returns PMF_ERR_CUDA; PMF_OK for cudaSuccess
+pmf_status cuda_err_at(cudaError_t e, const char *where);
 cudaError_t worker_occupancy(int tile_h, int *blocks_per_sm);
 
 }  // namespace pmf

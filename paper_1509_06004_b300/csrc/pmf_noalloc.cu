@@ -12,6 +12,7 @@
 // contents; each call re-initialises the parts that must start from zero.  Two
 // calls whose GPU work overlapped would race on the array, so calls are
 // serialised by a process-wide lock held until the call's stream work is done.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -29,10 +30,20 @@ namespace {
 
 constexpr size_t kScratchBytes = (size_t)PMF_NOALLOC_SCRATCH_MB << 20;
 constexpr int kMaxDevices = 64;
-constexpr int kTileH = 8;
+// solver knobs: the autotuner's choice for one-instance workloads (tile
+// height 4, pushes along columns and rows, 8 sweeps per visit, relabel
+// cadence 800 %, label slack 16)
+constexpr int kTileH = 4;
+constexpr int kPushOrder = 1;
+constexpr int kSweeps = 8;
+constexpr int kRelabelPct = 800;
+constexpr int kLabelSlack = 16;
 
 std::mutex g_lock;
 void *g_addr[kMaxDevices];   // device address of the array, per device, looked up once
+// test hook (pmf_testing_fail_noalloc_call): the n-th CUDA call of the next
+// pmf_solve_noalloc reports a failure instead of being made; 0 = none
+std::atomic<int> g_fail_at{0};
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -42,7 +53,8 @@ pmf_status scratch_address(int dev, char **out) {
     if (!g_addr[dev]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr) return PMF_ERR_CUDA;
+        if (e != cudaSuccess) return cuda_err_at(e, "pmf_solve_noalloc: cudaGetSymbolAddress");
+        if (p == nullptr) return cuda_err_at(cudaErrorInvalidSymbol, "pmf_solve_noalloc: cudaGetSymbolAddress");
         g_addr[dev] = p;
     }
     *out = static_cast<char *>(g_addr[dev]);
@@ -91,16 +103,42 @@ extern "C" PMF_API pmf_status pmf_solve_noalloc(int32_t H, int32_t W, const int3
     if (off > kScratchBytes) return PMF_ERR_OUT_OF_MEMORY;
 
     std::lock_guard<std::mutex> guard(g_lock);
+    const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int fail_at = g_fail_at.exchange(0);
+    int n_calls = 0;
+    cudaError_t e = cudaSuccess;
+    const char *where = "";
+    bool enqueued = false;   // stream work of this call may be in flight
+    // one CUDA call: skipped after a failure; the test hook may fail it
+    auto step = [&](const char *site, auto &&call) {
+        if (e != cudaSuccess) return;
+        if (++n_calls == fail_at) {
+            e = cudaErrorUnknown;
+            where = "pmf_solve_noalloc: injected failure";
+            return;
+        }
+        e = call();
+        if (e != cudaSuccess) where = site;
+    };
+    // an error return first waits for this call's queued work: the next call
+    // must not start while it could still touch the shared array
+    auto fail = [&]() -> pmf_status {
+        if (enqueued) (void)cudaStreamSynchronize(s);
+        return cuda_err_at(e, where);
+    };
+
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return PMF_ERR_CUDA;
+    step("pmf_solve_noalloc: cudaGetDevice", [&] { return cudaGetDevice(&dev); });
+    if (e != cudaSuccess) return fail();
     char *ws = nullptr;
     pmf_status st = scratch_address(dev, &ws);
     if (st != PMF_OK) return st;
     int n_sm = 0, bps = 0;
-    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1)
-        return PMF_ERR_CUDA;
+    step("pmf_solve_noalloc: cudaDeviceGetAttribute",
+         [&] { return cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev); });
+    if (e != cudaSuccess) return fail();
+    if (n_sm < 1) return cuda_err_at(cudaErrorInvalidDevice, "pmf_solve_noalloc: multiprocessor count");
     if (worker_occupancy(kTileH, &bps) != cudaSuccess || bps < 1) bps = 1;
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
     DevInst d;
     std::memset(&d, 0, sizeof(d));
@@ -138,8 +176,10 @@ extern "C" PMF_API pmf_status pmf_solve_noalloc(int32_t H, int32_t W, const int3
     P.n_tiles_total = n_tiles;
     P.n_leads_total = d.n_leads;
     P.max_lambdas = n_lambda;
-    P.sweeps = 8;
-    P.relabel_pct = 200;
+    P.sweeps = kSweeps;
+    P.chain_push = kPushOrder;
+    P.relabel_pct = kRelabelPct;
+    P.label_slack = kLabelSlack;
     P.tile_h = kTileH;
     P.poll_ns = 256;
     P.max_visits_per_tile = 2000;
@@ -148,30 +188,47 @@ extern "C" PMF_API pmf_status pmf_solve_noalloc(int32_t H, int32_t W, const int3
 
     // everything the solve reads before writing starts from zero; the rest is
     // written in full by the set-up kernels
-    cudaError_t e = cudaMemsetAsync(ws + o_flags, 0, sizeof(int32_t) * 2, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ws + o_glob, 0, sizeof(Globals), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ws + o_flows, 0, sizeof(int64_t) * n_lambda, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ws + o_dinst, &d, sizeof(d), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ws + o_lam, lambdas, sizeof(int32_t) * n_lambda, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_pad_image(P, 0, d, w_h, w_v, reinterpret_cast<int32_t *>(ws + o_flags), s);
-    if (e == cudaSuccess) e = launch_pad_terminals(P, 0, d, src0, slope, sink, s);
-    if (e == cudaSuccess) e = launch_reset(P, s);
-    if (e == cudaSuccess) e = launch_init(P, (int)PS, s);
-    if (e == cudaSuccess) e = launch_worker(P, bps * n_sm, s);
+    enqueued = true;
+    step("pmf_solve_noalloc: clear flags", [&] { return cudaMemsetAsync(ws + o_flags, 0, sizeof(int32_t) * 2, s); });
+    step("pmf_solve_noalloc: clear globals", [&] { return cudaMemsetAsync(ws + o_glob, 0, sizeof(Globals), s); });
+    step("pmf_solve_noalloc: clear flows",
+         [&] { return cudaMemsetAsync(ws + o_flows, 0, sizeof(int64_t) * n_lambda, s); });
+    step("pmf_solve_noalloc: descriptor",
+         [&] { return cudaMemcpyAsync(ws + o_dinst, &d, sizeof(d), cudaMemcpyHostToDevice, s); });
+    step("pmf_solve_noalloc: schedule", [&] {
+        return cudaMemcpyAsync(ws + o_lam, lambdas, sizeof(int32_t) * n_lambda, cudaMemcpyHostToDevice, s);
+    });
+    step("pmf_solve_noalloc: pad_image",
+         [&] { return launch_pad_image(P, 0, d, w_h, w_v, reinterpret_cast<int32_t *>(ws + o_flags), s); });
+    step("pmf_solve_noalloc: pad_terminals", [&] { return launch_pad_terminals(P, 0, d, src0, slope, sink, s); });
+    step("pmf_solve_noalloc: reset", [&] { return launch_reset(P, s); });
+    step("pmf_solve_noalloc: init", [&] { return launch_init(P, (int)PS, s); });
+    step("pmf_solve_noalloc: worker", [&] { return launch_worker(P, bps * n_sm, s); });
     InstState ist;
     Globals glob;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&ist, ws + o_ist, sizeof(ist), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&glob, ws + o_glob, sizeof(glob), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return PMF_ERR_CUDA;
+    step("pmf_solve_noalloc: read state",
+         [&] { return cudaMemcpyAsync(&ist, ws + o_ist, sizeof(ist), cudaMemcpyDeviceToHost, s); });
+    step("pmf_solve_noalloc: read globals",
+         [&] { return cudaMemcpyAsync(&glob, ws + o_glob, sizeof(glob), cudaMemcpyDeviceToHost, s); });
+    step("pmf_solve_noalloc: synchronise", [&] { return cudaStreamSynchronize(s); });
+    if (e != cudaSuccess) return fail();
+    enqueued = false;
     if (ist.status != PMF_OK) return (pmf_status)ist.status;
     if (glob.err || ist.phase != PH_DONE || ist.k < n_lambda) return PMF_ERR_NOT_CONVERGED;
 
     // outputs: flow values to the caller's host array, masks to its device buffer
-    e = cudaMemcpyAsync(flows, ws + o_flows, sizeof(int64_t) * n_lambda, cudaMemcpyDeviceToHost, s);
-    for (int k = 0; k < n_lambda && e == cudaSuccess; ++k)
-        e = cudaMemcpy2DAsync(masks + (size_t)k * H * W, W, ws + o_masks + (size_t)k * PS, pitch, W, H,
-                              cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    return e == cudaSuccess ? PMF_OK : PMF_ERR_CUDA;
+    enqueued = true;
+    step("pmf_solve_noalloc: copy flows", [&] {
+        return cudaMemcpyAsync(flows, ws + o_flows, sizeof(int64_t) * n_lambda, cudaMemcpyDeviceToHost, s);
+    });
+    for (int k = 0; k < n_lambda; ++k)
+        step("pmf_solve_noalloc: copy masks", [&] {
+            return cudaMemcpy2DAsync(masks + (size_t)k * H * W, W, ws + o_masks + (size_t)k * PS, pitch, W, H,
+                                     cudaMemcpyDeviceToDevice, s);
+        });
+    step("pmf_solve_noalloc: synchronise", [&] { return cudaStreamSynchronize(s); });
+    if (e != cudaSuccess) return fail();
+    return PMF_OK;
 }
+
+extern "C" PMF_API void pmf_testing_fail_noalloc_call(int32_t n) { g_fail_at.store(n > 0 ? n : 0); }

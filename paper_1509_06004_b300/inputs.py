@@ -155,6 +155,9 @@ class Instance:
     sink: np.ndarray         # int32 [H, W]
     lambdas: np.ndarray      # int32 [m], strictly increasing
     seed_origin: tuple[int, int] = (0, 0)
+    # for a piece of a split schedule: (index of the instance it was cut from,
+    # int array of the positions of its lambdas in that instance's schedule)
+    origin: tuple | None = None
 
 
 @dataclass
@@ -172,19 +175,26 @@ class Workload:
         return sum(self.images[i.image].H * self.images[i.image].W * len(i.lambdas)
                    for i in self.instances)
 
+    def _piece(self, i: int, inst: Instance, idx) -> Instance:
+        idx = np.asarray(idx, dtype=np.int64)
+        base = inst.origin
+        # a piece of a piece keeps pointing at the original schedule
+        o = (i, idx) if base is None else (base[0], base[1][idx])
+        return Instance(inst.image, inst.src0, inst.slope, inst.sink, inst.lambdas[idx].astype(np.int32),
+                        inst.seed_origin, o)
+
     def split_segments(self, segments: int) -> "Workload":
         """Every instance's schedule cut into ``segments`` consecutive pieces of
         equal length, each its own instance (warm-started inside a piece, cold
         at its first lambda).  segments = 1 is the workload itself; segments =
         schedule length is split_lambdas()."""
         out = Workload(self.name + (f"/seg{segments}" if segments > 1 else ""), list(self.images), [])
-        for inst in self.instances:
+        for i, inst in enumerate(self.instances):
             m = len(inst.lambdas)
             if m % segments:
                 raise ValueError(f"{segments} segments do not divide a schedule of {m}")
-            for part in np.split(inst.lambdas, segments):
-                out.instances.append(Instance(inst.image, inst.src0, inst.slope, inst.sink,
-                                              part.astype(np.int32), inst.seed_origin))
+            for part in np.split(np.arange(m), segments):
+                out.instances.append(self._piece(i, inst, part))
         return out
 
     def split_pieces(self, lengths) -> "Workload":
@@ -196,22 +206,66 @@ class Workload:
         if min(lengths) < 1:
             raise ValueError("pieces need at least one lambda")
         out = Workload(self.name + "/pieces" + "-".join(map(str, lengths)), list(self.images), [])
-        for inst in self.instances:
+        for i, inst in enumerate(self.instances):
             if sum(lengths) != len(inst.lambdas):
                 raise ValueError(f"pieces {lengths} do not cover a schedule of {len(inst.lambdas)}")
-            for part in np.split(inst.lambdas, np.cumsum(lengths)[:-1]):
-                out.instances.append(Instance(inst.image, inst.src0, inst.slope, inst.sink,
-                                              part.astype(np.int32), inst.seed_origin))
+            for part in np.split(np.arange(len(inst.lambdas)), np.cumsum(lengths)[:-1]):
+                out.instances.append(self._piece(i, inst, part))
+        return out
+
+    def split_interleaved(self, stride: int) -> "Workload":
+        """Every instance's schedule dealt round-robin into ``stride`` pieces:
+        piece j holds lambda_j, lambda_{j+stride}, lambda_{j+2*stride}, ...
+        Each piece starts cold at one of the schedule's ``stride`` smallest
+        lambdas and is warm-started along its own (coarser, still
+        nondecreasing) schedule, so neighbouring lambdas of one seed are solved
+        side by side.  stride = 1 is the workload itself."""
+        out = Workload(self.name + (f"/ilv{stride}" if stride > 1 else ""), list(self.images), [])
+        for i, inst in enumerate(self.instances):
+            m = len(inst.lambdas)
+            if not 1 <= stride <= m:
+                raise ValueError(f"stride {stride} outside [1, {m}]")
+            for j in range(stride):
+                out.instances.append(self._piece(i, inst, np.arange(j, m, stride)))
         return out
 
     def split_lambdas(self) -> "Workload":
         """The same solves with every (instance, lambda) as its own one-lambda
         instance (the lambda-concurrent form: no warm start between lambdas)."""
         out = Workload(self.name + "/lambda-split", list(self.images), [])
-        for inst in self.instances:
-            for lam in inst.lambdas:
-                out.instances.append(Instance(inst.image, inst.src0, inst.slope, inst.sink,
-                                              np.array([lam], dtype=np.int32), inst.seed_origin))
+        for i, inst in enumerate(self.instances):
+            for k in range(len(inst.lambdas)):
+                out.instances.append(self._piece(i, inst, [k]))
+        return out
+
+    def gather(self, results, n_instances: int | None = None):
+        """Results of a split workload ([(flows [m_i], masks [m_i, H, W])] per
+        piece, in this workload's instance order) put back per original
+        instance: a list of (flows [m], masks [m, H, W]).  Pieces without an
+        origin are their own original instance.  Every lambda of every
+        original instance must be covered exactly once."""
+        groups: dict[int, list] = {}
+        for j, (inst, (f, m)) in enumerate(zip(self.instances, results)):
+            oi, idx = inst.origin if inst.origin is not None else (j, np.arange(len(inst.lambdas)))
+            groups.setdefault(oi, []).append((idx, f, m))
+        n = n_instances if n_instances is not None else max(groups) + 1
+        out = []
+        for oi in range(n):
+            parts = groups[oi]
+            m_len = sum(len(idx) for idx, _, _ in parts)
+            f0, mk0 = parts[0][1], parts[0][2]
+            flows = np.zeros(m_len, dtype=np.asarray(f0).dtype)
+            masks = np.zeros((m_len,) + mk0.shape[1:], dtype=mk0.dtype)
+            seen = np.zeros(m_len, dtype=bool)
+            for idx, f, mk in parts:
+                if seen[idx].any():
+                    raise ValueError(f"lambda covered twice in instance {oi}")
+                seen[idx] = True
+                flows[idx] = f
+                masks[idx] = mk
+            if not seen.all():
+                raise ValueError(f"lambda not covered in instance {oi}")
+            out.append((flows, masks))
         return out
 
 

@@ -40,7 +40,7 @@ EXPORTS = ["pmf_workspace_size", "pmf_create_batch", "pmf_set_tuning", "pmf_get_
            "pmf_get_stats", "pmf_get_trace", "pmf_get_profile", "pmf_get_mask_layout",
            "pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error",
            "pmf_solve_noalloc", "pmf_get_flow_arcs", "pmf_set_cut_rule",
-           "pmf_set_slope_side"]
+           "pmf_set_slope_side", "pmf_testing_fail_noalloc_call"]
 
 
 class PmfError(RuntimeError):
@@ -137,10 +137,13 @@ def lib(path: str | None = None):
             L.pmf_version.restype = ctypes.c_char_p
             L.pmf_solve_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32p, i32, vp,
                                             ctypes.POINTER(ctypes.c_int64), vp]
+            L.pmf_testing_fail_noalloc_call.argtypes = [i32]
+            L.pmf_testing_fail_noalloc_call.restype = None
             L.pmf_last_error.argtypes = []
             L.pmf_last_error.restype = ctypes.c_char_p
             for name in EXPORTS:
-                if name not in ("pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error"):
+                if name not in ("pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error",
+                                "pmf_testing_fail_noalloc_call"):
                     getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib

@@ -33,8 +33,11 @@ def needs_swap(src0, slope, sink, lam: int) -> bool:
 
 def swapped_terminals(src0, slope, sink, lam: int):
     """Terminals of the exchanged problem at one lambda: (src0', slope', sink')
-    = (ct, 0, cs(lambda))."""
+    = (ct, 0, cs(lambda)).  cs(lambda) must lie in [0, 2^30] (the sink
+    capacities of the exchanged problem), else ValueError."""
     cs = np.asarray(src0, np.int64) + np.asarray(slope, np.int64) * int(lam)
+    if cs.size and (cs.max() > (1 << 30) or cs.min() < 0):
+        raise ValueError("source capacities at lambda must lie in [0, 2^30]")
     return (np.ascontiguousarray(sink, np.int32), np.zeros_like(np.asarray(sink, np.int32)),
             cs.astype(np.int32))
 

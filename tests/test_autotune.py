@@ -20,15 +20,47 @@ def test_coordinate_descent_finds_separable_minimum():
     target = {"segments": 4, "tile_h": 8, "push_order": 1, "sweeps": 16, "relabel_every": 400, "label_slack": 32,
               "relabel_extra": 256, "poll_ns": 1024}
 
-    def cost(w, s, k):
-        c = abs(np.log2(s) - np.log2(target["segments"]))
+    def cost(w, p, k):
+        assert p["interleave"] == 1 or p["segments"] == 1
+        c = abs(np.log2(p["segments"]) - np.log2(target["segments"])) + (p["interleave"] - 1)
         for name in autotune.SPACE:
             c += abs(autotune.SPACE[name].index(k[name]) - autotune.SPACE[name].index(target[name]))
         return 10.0 + c
 
     res = autotune.tune(wl, measure=cost, budget_s=30)
     assert {k: res[k] for k in target} == target
+    assert res["interleave"] == 1
     assert res["ms"] == 10.0
+
+
+def test_descent_picks_round_robin_pieces():
+    """A cost that favours dealing each schedule into three round-robin pieces
+    is found, and the plan batches the workload that way."""
+    wl = inputs.single_maxflow_64()
+    wl.instances[0].lambdas = np.arange(1, 13, dtype=np.int32)
+
+    def cost(w, p, k):
+        return 5.0 + abs(p["interleave"] - 3) + 0.5 * (p["segments"] - 1)
+
+    res = autotune.tune(wl, measure=cost, budget_s=30)
+    assert res["interleave"] == 3 and res["segments"] == 1
+    w = autotune.apply_plan(wl, res)
+    assert [list(i.lambdas) for i in w.instances] == [[1, 4, 7, 10], [2, 5, 8, 11], [3, 6, 9, 12]]
+    assert autotune.plan_name(res, 12) == "ilv3"
+
+
+def test_gather_restores_every_plan():
+    """Pieces of every plan put back per seed give the original schedules."""
+    wl = inputs.supergraph_480x320()
+    m = len(wl.instances[0].lambdas)
+    for p in autotune.plans_for(m):
+        w = autotune.apply_plan(wl, p)
+        fake = [(np.asarray(i.lambdas, np.int64) * 3 + i.origin[0] if i.origin else np.asarray(i.lambdas, np.int64) * 3,
+                 np.asarray(i.lambdas, np.uint8).reshape(-1, 1, 1)) for i in w.instances]
+        g = w.gather(fake, len(wl.instances))
+        for s, (f, mk) in enumerate(g):
+            assert np.array_equal(f, wl.instances[s].lambdas.astype(np.int64) * 3 + (s if (p["segments"] > 1 or p["interleave"] > 1) else 0))
+            assert np.array_equal(mk.ravel(), wl.instances[s].lambdas.astype(np.uint8))
 
 
 def test_cache_round_trip(tmp_path):

@@ -1,8 +1,7 @@
 """GPU tests beyond plain parity: batch invariance (Section 3.1's decomposition
 argument: each instance's minimum cut is the same alone or inside a larger
 batch), independence from the launch configuration, the batching modes, the
-input paths, full-size sampled parity at the benchmark's launch
-configuration, edge cases and every error status of the C ABI."""
+input paths, sampled parity on large images, edge cases and every error status of the C ABI."""
 import ctypes
 
 import numpy as np
@@ -89,6 +88,18 @@ def test_batching_modes_agree(P):
             f = np.concatenate([split[s * segs + j][0] for j in range(segs)])
             m = np.concatenate([split[s * segs + j][1] for j in range(segs)])
             assert np.array_equal(f, base[s][0]) and np.array_equal(m, base[s][1])
+
+
+@pytest.mark.parametrize("stride", [2, 3, 5, 8])
+def test_round_robin_pieces_agree(P, stride):
+    """Schedules dealt round-robin into pieces (piece j: lambda_j,
+    lambda_{j+stride}, ...; pieces of unequal length in one launch) give the
+    unsplit results once put back in schedule order."""
+    wl = _synthetic(24, 66, 101, 3, 8)
+    base = _solve(P, wl)
+    run = wl.split_interleaved(stride)
+    got = run.gather(_solve(P, run), len(wl.instances))
+    _same(base, got)
 
 
 @pytest.mark.parametrize("pieces", [[1, 7], [3, 5], [2, 1, 5], [5, 2, 1], [1, 1, 1, 1, 4]])
@@ -228,30 +239,9 @@ def test_repeated_solves_and_device_inputs(P):
 
 
 # ---------------------------------------------------------------------------
-# full-size parity at the benchmark's launch configuration (sampled)
+# large images (sampled; the benchmarked workloads are compared in full in
+# test_parity_bench_configs.py)
 # ---------------------------------------------------------------------------
-
-def test_supergraph_480x320_sampled_at_bench_configuration(P):
-    from paper_1509_06004_b300 import autotune
-    wl = inputs.supergraph_480x320()
-    c = autotune.cached(wl) or {"segments": 5, **autotune.DEFAULTS}
-    knobs = {k: c.get(k, v) for k, v in autotune.DEFAULTS.items()}
-    run = wl.split_segments(c["segments"]) if c["segments"] > 1 else wl
-    res = _solve(P, run, **knobs)
-    rng = np.random.default_rng(0)
-    for i in rng.choice(len(run.instances), size=4, replace=False):
-        inst = run.instances[i]
-        im = run.images[inst.image]
-        k = int(rng.integers(0, len(inst.lambdas)))
-        of, om = oracle.grid_solve(im.H, im.W, im.w_h, im.w_v, inst.src0, inst.slope, inst.sink,
-                                   [inst.lambdas[k]])
-        assert res[i][0][k] == of[0]
-        assert np.array_equal(res[i][1][k], om[0])
-    # properties that hold at any size: nested cuts and nondecreasing flows along each piece
-    for f, m in res:
-        assert np.all(np.diff(f) >= 0)
-        assert np.all(m[:-1] <= m[1:])
-
 
 def test_large_image_sampled(P):
     """A 770 x 1010 image (no side a multiple of the tile or strip sizes):

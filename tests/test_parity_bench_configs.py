@@ -1,0 +1,106 @@
+"""Parity with the CPU oracle at the benchmarked workloads, in the launch
+configurations the benchmark times them with.
+
+The property pinned is Section 2's exact cut: the maximum flow value and the
+maximal source set of every (seed, lambda) solve are unique, so every flow and
+every mask of the GPU path must equal the oracle's (each lambda solved from
+scratch by Dinic) element by element.
+
+* supergraph 480x320 (25 seeds x 20 lambdas): all 500 solves, batched by the
+  autotuner's plan for this GPU (the benchmark's default configuration);
+* uneven batch (64 images x 8 seeds x 16 lambdas, 8192 solves): the whole batch
+  in one launch at its own autotuned configuration; the oracle checks a fixed
+  subset that covers every image size: all 8 seeds x 16 lambdas of the first
+  image of each of the five sizes (images 0, 1, 4, 11 and 21: 640 solves);
+  every other solve is checked for nested masks and nondecreasing flows;
+* parametric 320x240 (one seed, 20 lambdas): all 20 steps as ONE warm-started
+  chain (the configuration's own mode: increasing lambdas with flow warm
+  start), and again as the benchmark's plan batches it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1509_06004_b300 import autotune, inputs
+
+pytestmark = pytest.mark.gpu
+
+# first image of each size in the uneven batch (sizes drawn by the generator)
+UNEVEN_SUBSET_IMAGES = (0, 1, 4, 11, 21)
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_06004_b300 import build, pmf
+    build.build()
+    return pmf
+
+
+def _solve_plan(P, wl, plan):
+    """Solve a workload batched by a plan (one launch); results per original
+    instance."""
+    run = autotune.apply_plan(wl, plan)
+    st, res = P.solve_workload(run, **autotune.knobs_of(plan))
+    assert all(s == P.PMF_OK for s in st), [P.status_string(s) for s in st if s]
+    return run.gather(res, len(wl.instances))
+
+
+def _compare(gpu, ora, idx):
+    for i, (of, om) in zip(idx, ora):
+        gf, gm = gpu[i]
+        assert np.array_equal(gf, of), (i, np.flatnonzero(gf != of)[:5], gf, of)
+        bad = np.argwhere(gm != om)
+        assert bad.size == 0, (i, bad[:10])
+
+
+def _invariants(res):
+    for f, m in res:
+        assert np.all(np.diff(f) >= 0)
+        assert np.all(m[:-1] <= m[1:])
+
+
+def test_uneven_subset_covers_every_size():
+    """The stated subset holds the first image of each of the five sizes."""
+    wl = inputs.uneven_batch()
+    firsts = {}
+    for i, im in enumerate(wl.images):
+        firsts.setdefault((im.H, im.W), i)
+    assert tuple(sorted(firsts.values())) == UNEVEN_SUBSET_IMAGES
+    assert len(firsts) == len(inputs.UNEVEN_SIZES)
+
+
+def test_supergraph_480x320_all_500_solves_at_bench_configuration(P):
+    wl = inputs.supergraph_480x320()
+    plan = autotune.bench_plan(wl)
+    gpu = _solve_plan(P, wl, plan)
+    ora = oracle.solve_workload(wl)
+    assert sum(len(f) for f, _ in ora) == 500
+    _compare(gpu, ora, range(len(wl.instances)))
+    _invariants(gpu)
+
+
+def test_uneven_64_at_its_own_configuration(P):
+    wl = inputs.uneven_batch()
+    assert wl.n_solves == 8192
+    plan = autotune.bench_plan(wl)
+    gpu = _solve_plan(P, wl, plan)
+    idx = [i for i, inst in enumerate(wl.instances) if inst.image in UNEVEN_SUBSET_IMAGES]
+    assert len(idx) == 5 * 8
+    ora = oracle.solve_workload(wl, instances=idx)
+    _compare(gpu, ora, idx)
+    _invariants(gpu)
+
+
+@pytest.mark.parametrize("batching", ["warm-chain", "bench-plan"])
+def test_parametric_320x240_all_20_steps(P, batching):
+    wl = inputs.parametric_320x240()
+    plan = autotune.bench_plan(wl)
+    if batching == "warm-chain":
+        plan = dict(plan, segments=1, interleave=1)
+    gpu = _solve_plan(P, wl, plan)
+    ora = oracle.solve_workload(wl)
+    _compare(gpu, ora, [0])
+    _invariants(gpu)
