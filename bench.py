@@ -69,6 +69,10 @@ def mode_text(mode):
     if mode.startswith("ilv"):
         return (f"each seed's schedule dealt round-robin into {mode[3:]} warm-started pieces "
                 "(piece j: lambda_j, lambda_j+P, ...)")
+    if mode.startswith("fork"):
+        seg, lead = mode[4:].split("x")
+        return (f"each seed's schedule in {seg} consecutive pieces, each after the first forked from a copy of "
+                f"the previous piece's state {lead} steps before that piece's end")
     return mode
 
 
@@ -82,6 +86,9 @@ def parse_mode(mode: str, m: int):
         return {"segments": int(mode[3:]), "interleave": 1}
     if mode.startswith("ilv"):
         return {"segments": 1, "interleave": int(mode[3:])}
+    if mode.startswith("fork"):
+        seg, lead = mode[4:].split("x")
+        return {"segments": int(seg), "interleave": 1, "fork": int(lead)}
     return None
 
 
@@ -198,7 +205,7 @@ def resolve_mode(args, wl, dev, tuning0):
     c = autotune.cached(wl, dev.index)
     if c is not None and not tuning0:
         p = autotune.bench_plan(wl, dev.index)
-        return ({"segments": p["segments"], "interleave": p["interleave"]}, autotune.knobs_of(p),
+        return ({"segments": p["segments"], "interleave": p["interleave"], "fork": p["fork"]}, autotune.knobs_of(p),
                 {"source": "autotune cache", "class": autotune.workload_class(wl), "tuned_ms": c.get("ms")})
     divs = autotune.divisors(m)
     cands = sorted({1, divs[len(divs) // 2], m})
@@ -529,8 +536,10 @@ def e2e(args, wl, b, lam, dev, stream, pmf, world):
 
 def serving_bench(args, dev):
     """Poisson request stream (one image of random size, its seeds and lambda
-    schedule per request) served with continuous batching, against serving
-    the same stream one request at a time on the whole GPU."""
+    schedule per request) served with continuous batching into one running
+    server kernel, against the same stream one request at a time on the same
+    server, and against one launch per request with a static share of the SMs
+    (slots of their own)."""
     import torch
     from paper_1509_06004_b300 import serving
     # the first serving_warmup requests of the stream are served but left out
@@ -542,11 +551,16 @@ def serving_bench(args, dev):
     out = {"rate_per_s": args.serving_rate, "requests": args.serving_requests, "warmup_requests": nw,
            "max_side": args.serving_max_side, "budget_bytes": args.serving_budget,
            "pixel_solves": sum(r.workload.pixel_solves for r in reqs[nw:])}
-    for name, slots in (("continuous", args.serving_slots), ("one_at_a_time", 1)):
-        serving.serve(warm, slots=slots, budget_bytes=args.serving_budget, device=dev.index)
-        st = serving.serve(reqs, slots=slots, budget_bytes=args.serving_budget, device=dev.index)
+    legs = [("continuous", args.serving_slots, True), ("one_at_a_time", 1, True)]
+    if not args.no_serving_batches:
+        legs.append(("continuous_launch_per_request", 4, False))
+    for name, slots, live in legs:
+        serving.serve(warm, slots=slots, budget_bytes=args.serving_budget, device=dev.index, live=live)
+        st = serving.serve(reqs, slots=slots, budget_bytes=args.serving_budget, device=dev.index, live=live)
         out[name] = st.summary(skip=nw)
         out[name]["slots"] = slots
+        out[name]["path"] = ("one running server kernel, requests admitted into its device queue" if live
+                             else "one batch and persistent launch per request, a static share of the SMs each")
         torch.cuda.empty_cache()
     return out
 
@@ -607,7 +621,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="supergraph-480x320")
-    ap.add_argument("--mode", default="auto", help="auto | m2 | m1 | seg<N> | ilv<N>")
+    ap.add_argument("--mode", default="auto", help="auto | m2 | m1 | seg<N> | ilv<N> | fork<N>x<lead>")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tile-h", type=int, default=0)
     ap.add_argument("--sweeps", type=int, default=0)
@@ -627,7 +641,9 @@ def main(argv=None):
     ap.add_argument("--serving-rate", type=float, default=50.0)
     ap.add_argument("--serving-warmup", type=int, default=0, help="leading requests left out of the latencies")
     ap.add_argument("--serving-max-side", type=int, default=800)
-    ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-slots", type=int, default=8, help="requests admitted at once")
+    ap.add_argument("--no-serving-batches", action="store_true",
+                    help="skip the leg with one launch per request")
     ap.add_argument("--serving-budget", type=int, default=64 << 30)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":

@@ -227,6 +227,25 @@ PMF_API pmf_status pmf_set_cut_rule(pmf_batch *b, int32_t inst, int32_t rule);
  * for a bad instance or side. */
 PMF_API pmf_status pmf_set_slope_side(pmf_batch *b, int32_t inst, int32_t side);
 
+/* lambda-state copies (Section 3.1's supergraphs mix problems of one seed at
+ * several lambdas; GGT's warm start lets each start from an earlier one's
+ * flow): instance child starts from instance parent's state as it is once the
+ * parent has certified step parent_step of its schedule, instead of from the
+ * zero flow.  At that point, between the parent's steps, the parent's strips
+ * copy its flow, labels, excess and terminal capacities into the child (the
+ * child's own terminals are not used), the parent goes on with its next
+ * lambda and the child with the warm start from the parent's lambda to its
+ * own first lambda, so the two run side by side.  Both must be instances of
+ * the same image, with the same slope side and cut rule; a parent has at most
+ * one child (which may itself be a parent).  The solve checks that the
+ * parent's schedule has step parent_step, that the child's first lambda is
+ * not below the parent's lambda there (else PMF_ERR_NOT_MONOTONE) and that no
+ * chain of forks closes on itself.  A child whose parent fails before forking
+ * it finishes with the parent's status.  parent = -1 removes child's fork.
+ * Takes effect at the next solve.  PMF_ERR_INVALID_ARG for bad indices, a
+ * parent of another image, or a parent that already has another child. */
+PMF_API pmf_status pmf_set_fork(pmf_batch *b, int32_t child, int32_t parent, int32_t parent_step);
+
 /* Solve every instance at every lambda of its schedule.  lambdas is a host
  * array [n_inst][n_lambda] (n_lambda <= max_lambdas), nondecreasing along each
  * row (else PMF_ERR_NOT_MONOTONE, nothing launched).  Asynchronous on
@@ -322,6 +341,56 @@ PMF_API pmf_status pmf_get_profile(pmf_batch *b, uint64_t *out);
 PMF_API pmf_status pmf_get_flow_arcs(pmf_batch *b, int32_t inst, int32_t *f_h, int32_t *f_v, int32_t *f_s,
                                      int32_t *f_t);
 
+/* ------------------------------------------------------------------------ */
+/* Exact parametric search (Section 2.1: finding every breakpoint of the      */
+/* parametric minimum cut is the ideal the paper names; its preset lambda     */
+/* schedules approximate it).  Two device helpers; the search itself          */
+/* (parametric.exact_breakpoints in the Python package) solves the problems   */
+/* they build with the batch entry points.                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Capacity lines of cuts (Section 2's cut cost as a function of lambda): for
+ * each of n_masks source sets S_k = masks[k] | base (1 = s side; base may be
+ * NULL), cap_{S_k}(lambda) = a_k + b_k * lambda with
+ *   a_k = sum_{p not in S_k} src0(p) + sum_{p in S_k} sink(p)
+ *         + sum over 4-neighbour pairs split by S_k of their capacity,
+ *   b_k = sum_{p not in S_k} slope(p).
+ * All arrays are DEVICE pointers: w_h, w_v, src0, slope, sink are H*W int32
+ * (row-major, as for pmf_set_capacities / pmf_set_terminals), base is H*W
+ * bytes, masks n_masks*H*W bytes ([k][y][x]); lines receives 2*n_masks int64
+ * (a_k, b_k); union_out (may be NULL) receives the sets S_k as n_masks*H*W
+ * bytes.  Asynchronous on cuda_stream.  PMF_ERR_INVALID_ARG for a NULL
+ * pointer, a bad size or n_masks outside [1, 65535]; PMF_ERR_CUDA if the
+ * launch fails. */
+PMF_API pmf_status pmf_cut_lines(int32_t H, int32_t W, const int32_t *w_h, const int32_t *w_v,
+                                 const int32_t *src0, const int32_t *slope, const int32_t *sink,
+                                 const uint8_t *base, const uint8_t *masks, int32_t n_masks,
+                                 uint8_t *union_out, int64_t *lines, void *cuda_stream);
+
+/* The problem restricted to the pixels between two nested source sets
+ * s1 <= s2 (DEVICE masks of H*W bytes, 1 = s side) at lambda = p / q, scaled
+ * by q so that every capacity is an integer.  Pixels of D = s2 \ s1 keep their
+ * pair capacities to each other; a pixel's pairs into s1 join its source
+ * capacity and its pairs into the complement of s2 its sink capacity; every
+ * other pixel gets no arcs but a sink capacity of 1 (no flow passes it, and it
+ * is never in the maximal source set).  Outputs (DEVICE, H*W int32 each):
+ * w_h_out, w_v_out (pairs inside D, times q), src0_out = q*(src0 + pairs
+ * from s1) + p*slope, sink_out = q*(sink + pairs out of s2); solve them with
+ * slope 0.  sums (DEVICE, 4 int64): [0] sum of src0_out, [1] sum of
+ * sink_out over D, [2] pixels whose scaled capacities exceed PMF_INF or
+ * PMF_MAX_PAIRWISE (their outputs are zeroed and the problem must not be
+ * used), [3] pixels in D.  Every cut between s1 and s2 costs a constant plus
+ * the restricted problem's cut, so when s1 and s2 are maximal minimum cuts at
+ * lambda_1 <= p/q <= lambda_2, the restricted problem's maximal source set
+ * joined with s1 is the maximal minimum cut at p/q.  Asynchronous on
+ * cuda_stream.  PMF_ERR_INVALID_ARG for a NULL pointer, a bad size, q < 1,
+ * p < 0 or p, q above 2^31. */
+PMF_API pmf_status pmf_restrict_between(int32_t H, int32_t W, const int32_t *w_h, const int32_t *w_v,
+                                        const int32_t *src0, const int32_t *slope, const int32_t *sink,
+                                        const uint8_t *s1, const uint8_t *s2, int64_t p, int64_t q,
+                                        int32_t *w_h_out, int32_t *w_v_out, int32_t *src0_out,
+                                        int32_t *sink_out, int64_t *sums, void *cuda_stream);
+
 /* Counters of the last solve for one instance, after pmf_sync. */
 PMF_API pmf_status pmf_get_stats(pmf_batch *b, int32_t inst, pmf_stats *out);
 
@@ -334,6 +403,88 @@ PMF_API pmf_status pmf_get_mask_layout(pmf_batch *b, int32_t inst, const uint8_t
 PMF_API void pmf_destroy_batch(pmf_batch *b);
 
 PMF_API const char *pmf_status_string(pmf_status s);
+
+/* ------------------------------------------------------------------------ */
+/* Server: continuous batching into one running kernel (Section 3.3.1's       */
+/* dynamic scheduling, where each server takes the next problem as soon as it */
+/* is free, and Section 3.3.2's overlap of one request's transfers with       */
+/* another's computation).  A server owns n_slots instance slots, each able   */
+/* to hold one instance of up to max_h x max_w pixels and max_lambdas         */
+/* lambdas, and ONE persistent kernel that solves whatever is in its device   */
+/* work queue.  The host loads a request's instances into free slots (copies  */
+/* on a separate stream, while the kernel runs) and posts them; an idle       */
+/* worker of the running kernel takes the posted slots from a mailbox in      */
+/* mapped host memory, sets them up on the device and queues their work into  */
+/* the same queue every running instance uses.  Finished slots are flagged in */
+/* mapped host memory (pmf_server_poll) and read back while the others run.   */
+/* No call allocates or synchronises the device while the kernel runs.        */
+/* ------------------------------------------------------------------------ */
+typedef struct pmf_server pmf_server;   /* opaque, owned by the library */
+
+typedef struct {
+    int32_t n_slots;         /* instance slots, 1 .. 4096 */
+    int32_t max_h, max_w;    /* largest image a slot holds */
+    int32_t max_lambdas;     /* longest schedule a slot holds */
+    int32_t device;          /* CUDA device ordinal */
+} pmf_server_desc;
+
+/* Device workspace bytes of a server (host-only call). */
+PMF_API pmf_status pmf_server_workspace_size(const pmf_server_desc *desc, size_t *bytes);
+
+/* Create a server over a caller-owned device workspace of at least
+ * pmf_server_workspace_size() bytes (256-byte aligned).  Allocates a few pinned
+ * and mapped host buffers and two streams of its own.  PMF_ERR_OUT_OF_MEMORY
+ * if the workspace is too small. */
+PMF_API pmf_status pmf_server_create(const pmf_server_desc *desc, void *dev_workspace, size_t bytes,
+                                     pmf_server **out);
+
+/* Solver knobs of the server kernel (as pmf_set_tuning; the server runs tile
+ * height 4 with pushes along columns and rows, so tile_h must be 0 or 4,
+ * push_order is ignored and mode must be 0).  Only before pmf_server_start. */
+PMF_API pmf_status pmf_server_set_tuning(pmf_server *s, const pmf_tuning *t);
+
+/* Launch the server kernel (it runs until pmf_server_stop, or at most
+ * max_seconds, after which it stops with PMF_ERR_NOT_CONVERGED for whatever
+ * is unfinished).  Every slot starts free. */
+PMF_API pmf_status pmf_server_start(pmf_server *s, double max_seconds);
+
+/* Load one instance into a free slot (Section 2's grid graph and Section
+ * 2.1's schedule, as for pmf_set_capacities / pmf_set_terminals /
+ * pmf_solve_schedule): HOST arrays of H*W int32 (row-major) and n_lambda
+ * nondecreasing lambdas (else PMF_ERR_NOT_MONOTONE).  image_slot == slot:
+ * w_h, w_v are this slot's image; image_slot != slot: the instance uses the
+ * image loaded into image_slot (w_h, w_v may be NULL), which must then stay
+ * loaded, posted or unread until this slot has been read.  Capacities are
+ * checked on the device when the instance starts; a bad one is reported by
+ * pmf_server_read as by pmf_sync.  The copies run on the server's copy stream
+ * while the kernel runs.  PMF_ERR_NOT_READY for a slot posted and not yet
+ * read; PMF_ERR_INVALID_ARG for a bad slot, size or pointer. */
+PMF_API pmf_status pmf_server_load(pmf_server *s, int32_t slot, int32_t image_slot, int32_t H, int32_t W,
+                                   const int32_t *w_h, const int32_t *w_v, const int32_t *src0,
+                                   const int32_t *slope, const int32_t *sink, const int32_t *lambdas,
+                                   int32_t n_lambda);
+
+/* Admit loaded slots into the running kernel: waits for their copies, then
+ * posts them to the mailbox.  PMF_ERR_INVALID_ARG if the server is not running
+ * or a slot is not loaded. */
+PMF_API pmf_status pmf_server_post(pmf_server *s, const int32_t *slots, int32_t n);
+
+/* Which posted slots have finished, without waiting: done[i] = 1 (host array
+ * of n_slots bytes, may be NULL); *n_done (may be NULL) counts them. */
+PMF_API pmf_status pmf_server_poll(pmf_server *s, uint8_t *done, int32_t *n_done);
+
+/* Read a finished slot's results into HOST buffers: masks n_lambda*H*W bytes
+ * ([k][y][x], 1 = source side: the maximal minimum cut) and flows n_lambda
+ * int64, then free the slot.  Returns the instance's status (a failed one
+ * leaves the buffers untouched); PMF_ERR_NOT_READY before it has finished. */
+PMF_API pmf_status pmf_server_read(pmf_server *s, int32_t slot, uint8_t *masks, int64_t *flows);
+
+/* End the server kernel once every posted slot has finished, and wait for it.
+ * PMF_ERR_NOT_CONVERGED if it had stopped on a watchdog or its time limit. */
+PMF_API pmf_status pmf_server_stop(pmf_server *s);
+
+/* Stop the kernel if it runs and release the server's host side. */
+PMF_API void pmf_server_destroy(pmf_server *s);
 
 /* ------------------------------------------------------------------------ */
 /* Solve without allocating (the paper has no counterpart: this entry point   */

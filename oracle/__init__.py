@@ -13,6 +13,12 @@ Contents
   * ``grid_solve_many``  many grid (instance, lambda) jobs on a thread pool.
   * ``brute_force_*``    enumeration of every s-t cut of a graph with at most
                          16 non-terminal nodes (numpy, exact).
+  * ``grid_solve_rational``  one grid instance at a rational lambda = p/q,
+                         exact (every capacity times q).
+  * ``cut_line``         the cost of a given cut as a line a + b*lambda.
+  * ``brute_force_breakpoints``  every breakpoint of the minimum cut value
+                         F(lambda) on a range, by enumerating all cuts of a
+                         grid of at most 16 pixels (exact fractions).
   * ``grid_flow_value``  checks that per-arc flows on a grid form a feasible
                          s-t flow (capacity bounds and conservation) and
                          returns its value; ``grid_arc_flows`` gives such
@@ -301,6 +307,98 @@ def brute_force_grid(H, W, w_h, w_v, src0, slope, sink, lam):
     for p in range(N):
         union[p] = 1 if np.any((arg >> p) & 1) else 0
     return best, union.reshape(H, W), len(arg)
+
+
+# ----------------------------------------------------------------------------
+# the parametric cut at rational lambda and its breakpoints (Section 2.1)
+# ----------------------------------------------------------------------------
+
+def _arcs_line(H, W, w_h, w_v, src0, slope, sink):
+    """The arc list with each capacity as a line c0 + c1*lambda."""
+    tail, head, c0 = grid_arcs(H, W, w_h, w_v, src0, slope, sink, 0)
+    _, _, cl = grid_arcs(H, W, w_h, w_v, src0, slope, sink, 1)
+    return tail, head, c0, cl - c0
+
+
+def grid_solve_rational(H, W, w_h, w_v, src0, slope, sink, p: int, q: int, algo: str = "dinic"):
+    """Maximum flow and maximal source set of one grid instance at lambda =
+    p / q (q >= 1), exactly: every arc capacity c0 + c1*lambda is multiplied
+    by q, giving the integer q*c0 + p*c1; scaling all capacities by q scales
+    every cut's cost by q, so the minimum cuts are the same and the flow value
+    is q * F(p/q).  Returns (q * F(p/q), mask uint8 [H, W], 1 = source side)."""
+    p, q = int(p), int(q)
+    if q < 1:
+        raise ValueError("q >= 1")
+    tail, head, c0, c1 = _arcs_line(H, W, w_h, w_v, src0, slope, sink)
+    cap = q * c0 + p * c1
+    N = H * W
+    val, _, reach = maxflow(N + 2, tail, head, cap, N, N + 1, algo)
+    return val, (1 - reach[:N]).astype(np.uint8).reshape(H, W)
+
+
+def cut_line(H, W, w_h, w_v, src0, slope, sink, mask):
+    """(a, b) with a + b*lambda = the cost of the s-t cut whose s side is s
+    plus the pixels with mask = 1 (Section 2: the total capacity of the arcs
+    from the s side to the t side), read off the arc list."""
+    tail, head, c0, c1 = _arcs_line(H, W, w_h, w_v, src0, slope, sink)
+    N = H * W
+    side = np.concatenate([np.asarray(mask, np.uint8).ravel() != 0, [True, False]])
+    cut = side[tail] & ~side[head]
+    return int(c0[cut].sum()), int(c1[cut].sum())
+
+
+def brute_force_breakpoints(H, W, w_h, w_v, src0, slope, sink, lo, hi):
+    """Every breakpoint of F(lambda) = min over cuts of their cost on [lo, hi]
+    for a grid of at most 16 pixels, by enumeration.  Each cut's cost is a
+    line a_S + b_S*lambda (Section 2's cut cost with cs = src0 + slope*lambda),
+    so F is their lower envelope.  Walking up from lo, the line in force is
+    the one of least slope among those of least value, and the next breakpoint
+    is the nearest crossing with a line of smaller slope.  Returns
+    (breakpoints [Fraction] in (lo, hi], masks uint8 [r+1, H, W], lines
+    [(a, b)]): the maximal source set (union of the minimisers) on each piece,
+    from the one at lo on."""
+    from fractions import Fraction
+    N = H * W
+    assert N <= 16
+    i64 = lambda a: np.asarray(a, np.int64).reshape(H, W)
+    w_h, w_v, s0, sl, ct = i64(w_h), i64(w_v), i64(src0), i64(slope), i64(sink)
+    S = np.arange(1 << N, dtype=np.int64)
+    on = np.stack([(S >> p) & 1 for p in range(N)]).reshape(H, W, -1)    # 1 = s side
+    off = 1 - on
+    a = (s0[..., None] * off).sum(axis=(0, 1)) + (ct[..., None] * on).sum(axis=(0, 1))
+    x1, x2 = on[:, :-1], on[:, 1:]
+    a += (w_h[:, :-1, None] * (x1 * (1 - x2) + x2 * (1 - x1))).sum(axis=(0, 1))
+    y1, y2 = on[:-1, :], on[1:, :]
+    a += (w_v[:-1, :, None] * (y1 * (1 - y2) + y2 * (1 - y1))).sum(axis=(0, 1))
+    b = (sl[..., None] * off).sum(axis=(0, 1))
+    lines = sorted({(int(x), int(y)) for x, y in zip(a, b)})
+
+    def union_of(line):
+        sel = np.nonzero((a == line[0]) & (b == line[1]))[0]
+        m = np.zeros(N, np.uint8)
+        for p in range(N):
+            m[p] = 1 if np.any((sel >> p) & 1) else 0
+        return m.reshape(H, W)
+
+    lam = Fraction(lo)
+    val = min(x + y * lam for x, y in lines)
+    cur = min((l for l in lines if l[0] + l[1] * lam == val), key=lambda l: l[1])
+    bps, pieces = [], [cur]
+    while True:
+        nxt = None
+        for l in lines:
+            if l[1] < cur[1]:
+                x = Fraction(l[0] - cur[0], cur[1] - l[1])
+                if x > lam and (nxt is None or x < nxt):
+                    nxt = x
+        if nxt is None or nxt > hi:
+            break
+        lam = nxt
+        val = cur[0] + cur[1] * lam
+        cur = min((l for l in lines if l[0] + l[1] * lam == val), key=lambda l: l[1])
+        bps.append(lam)
+        pieces.append(cur)
+    return bps, np.stack([union_of(l) for l in pieces]), pieces
 
 
 # ----------------------------------------------------------------------------

@@ -12,6 +12,9 @@ instance count and schedule length:
 * ``interleave`` — each seed's schedule is dealt round-robin into this many
   pieces (piece j: lambda_j, lambda_{j+P}, ...): every piece starts cold at one
   of the smallest lambdas and neighbouring lambdas of a seed run side by side;
+* ``fork`` — with ``segments`` > 1: each piece after a seed's first starts
+  from a copy of the previous piece's state (pmf_set_fork) taken ``fork``
+  steps before that piece's end, instead of cold (-1 = cold pieces);
 * ``tile_h`` (rows per tile), ``push_order`` (pushes from the sweep's starting
   state, or along columns and rows), ``sweeps`` (push/relabel sweeps per tile visit),
   ``relabel_every`` (visit budget of a push/relabel phase, percent of its
@@ -58,7 +61,10 @@ def apply_plan(wl, plan: dict):
     if il > 1:
         w = w.split_interleaved(il)
     seg = int(plan.get("segments", 1) or 1)
-    if seg > 1:
+    fork = int(plan.get("fork", -1))
+    if seg > 1 and fork >= 0:
+        w = w.split_forked(seg, fork)
+    elif seg > 1:
         w = w.split_segments(seg)
     return w
 
@@ -72,8 +78,11 @@ def plan_name(plan: dict, m: int) -> str:
     """Short name of a batching plan for a schedule of m lambdas: m2 (one
     warm chain per seed), m1 (every (seed, lambda) cold), segN, ilvN."""
     seg, il = int(plan.get("segments", 1) or 1), int(plan.get("interleave", 1) or 1)
+    fork = int(plan.get("fork", -1))
     if il > 1:
         return f"ilv{il}" + (f"-seg{seg}" if seg > 1 else "")
+    if seg > 1 and fork >= 0:
+        return f"fork{seg}x{fork}"
     return "m2" if seg == 1 else ("m1" if seg == m else f"seg{seg}")
 
 
@@ -82,7 +91,7 @@ def bench_plan(wl, device: int = 0) -> dict:
     cached choice for this GPU and workload class, else the defaults with one
     warm chain per seed."""
     c = cached(wl, device)
-    out = {"segments": 1, "interleave": 1, **DEFAULTS}
+    out = {"segments": 1, "interleave": 1, "fork": -1, **DEFAULTS}
     if c is not None:
         for k in out:
             if k in c:
@@ -167,8 +176,16 @@ INTERLEAVE = [2, 3, 4, 5, 6, 8, 10]
 def plans_for(m: int) -> list[dict]:
     """Batching plans tried for a schedule of m lambdas: consecutive pieces
     (every divisor of m) and round-robin pieces (a few strides)."""
-    out = [{"segments": d, "interleave": 1} for d in divisors(m)]
-    out += [{"segments": 1, "interleave": p} for p in INTERLEAVE if p < m]
+    out = [{"segments": d, "interleave": 1, "fork": -1} for d in divisors(m)]
+    out += [{"segments": 1, "interleave": p, "fork": -1} for p in INTERLEAVE if p < m]
+    # forked pieces: each piece after the first starts from its predecessor's
+    # state, taken right after the predecessor's first step or halfway
+    for d in divisors(m):
+        if 1 < d < m:
+            L = m // d
+            for lead in sorted({L - 1, L // 2}):
+                if lead >= 1:
+                    out.append({"segments": d, "interleave": 1, "fork": lead})
     return out
 
 

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpmf.so")
 
-SOURCES = ["pmf_kernels.cu", "pmf_api.cpp", "pmf_noalloc.cu"]
+SOURCES = ["pmf_kernels.cu", "pmf_api.cpp", "pmf_noalloc.cu", "pmf_param.cu"]
 HEADERS = [os.path.join(CSRC, "pmf_internal.h"), os.path.join(INCLUDE, "pmf.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

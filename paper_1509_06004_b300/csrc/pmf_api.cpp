@@ -4,6 +4,7 @@
 // replayed), and reading back results.  Every step of the solve itself runs in
 // the kernels of pmf_kernels.cu.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -199,6 +200,7 @@ struct pmf_batch {
     float worker_ms_rounds = 0.f;
     bool in_flight = false;
     bool solved = false;
+    bool forks_changed = false;            // pmf_set_fork since the last geometry upload
     std::vector<int32_t> n_lam;            // schedule length of each instance in the last solve
     std::vector<DevInst> dinst;            // host copy of the descriptors
     // pinned host mirrors
@@ -273,19 +275,26 @@ pmf_status refresh_geometry(pmf_batch *b, cudaStream_t s) {
     }
     // the first relabel strips enter the queue largest instance first (a
     // longest-processing-time order: the biggest grids start earliest, so the
-    // small ones fill in at the end instead of a big one running alone)
+    // small ones fill in at the end instead of a big one running alone);
+    // forked instances, which wait for their parent, are numbered last
     std::vector<int> order(b->desc.n_inst);
     for (int i = 0; i < b->desc.n_inst; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int c) { return b->dinst_h[a].n_tiles > b->dinst_h[c].n_tiles; });
-    int lbase = 0;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        const bool wa = b->dinst_h[a].fork_parent >= 0, wc = b->dinst_h[c].fork_parent >= 0;
+        if (wa != wc) return wc;
+        return b->dinst_h[a].n_tiles > b->dinst_h[c].n_tiles;
+    });
+    int lbase = 0, queued = 0;
     for (int i : order) {
         b->dinst_h[i].lead_base = lbase;
         b->dinst[i].lead_base = lbase;
         lbase += b->dinst_h[i].n_leads;
+        if (b->dinst_h[i].fork_parent < 0) queued = lbase;
     }
     b->P.n_tiles_total = base;
     b->P.n_leads_total = lbase;
+    b->P.n_leads_queued = queued;
+    b->forks_changed = false;
     b->P.tile_h = th;
     return cuda_err(cudaMemcpyAsync(b->ws + b->L.dev_inst, b->dinst_h, sizeof(DevInst) * b->desc.n_inst,
                                     cudaMemcpyHostToDevice, s));
@@ -378,6 +387,10 @@ pmf_status pmf_create_batch(const pmf_batch_desc *desc, void *dev_workspace, siz
     b->device = desc->device;
     b->setup_stream = (cudaStream_t)cuda_stream;
     b->dinst.resize(desc->n_inst);
+    for (DevInst &d : b->dinst) {
+        std::memset(&d, 0, sizeof(d));
+        d.fork_parent = d.fork_child = d.fork_k = -1;
+    }
     b->n_lam.assign(desc->n_inst, 0);
     apply_defaults(&b->tune);
     cudaError_t e = cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
@@ -573,6 +586,31 @@ pmf_status pmf_set_slope_side(pmf_batch *b, int32_t inst, int32_t side) {
     return cuda_err(e);
 }
 
+pmf_status pmf_set_fork(pmf_batch *b, int32_t child, int32_t parent, int32_t parent_step) {
+    if (!b || child < 0 || child >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
+    if (parent >= 0) {
+        if (parent >= b->desc.n_inst || parent == child || parent_step < 0) return PMF_ERR_INVALID_ARG;
+        if (b->inst_image[parent] != b->inst_image[child]) return PMF_ERR_INVALID_ARG;
+        const int other = b->dinst[parent].fork_child;
+        if (other >= 0 && other != child) return PMF_ERR_INVALID_ARG;   // one child per parent
+    }
+    DeviceGuard dg(b->device);
+    if (b->in_flight) { cudaEventSynchronize(b->done); b->in_flight = false; }
+    const int old = b->dinst[child].fork_parent;
+    if (old >= 0) {
+        b->dinst[old].fork_child = -1;
+        b->dinst[old].fork_k = -1;
+    }
+    b->dinst[child].fork_parent = parent >= 0 ? parent : -1;
+    if (parent >= 0) {
+        b->dinst[parent].fork_child = child;
+        b->dinst[parent].fork_k = parent_step;
+    }
+    b->forks_changed = true;   // uploaded with the descriptors at the next solve
+    b->solved = false;
+    return PMF_OK;
+}
+
 pmf_status pmf_set_terminals(pmf_batch *b, int32_t inst, const int32_t *src0, const int32_t *slope,
                              const int32_t *sink, int on_device) {
     if (!b || !src0 || !slope || !sink || inst < 0 || inst >= b->desc.n_inst) return PMF_ERR_INVALID_ARG;
@@ -620,6 +658,26 @@ static pmf_status solve_impl(pmf_batch *b, const int32_t *lambdas, const int32_t
     for (int i = 0; i < b->desc.n_inst; ++i)
         for (int k = 1; k < len(i); ++k)
             if (lambdas[(size_t)i * stride + k] < lambdas[(size_t)i * stride + k - 1]) return PMF_ERR_NOT_MONOTONE;
+    // forks: the parent has the step it forks at, the child's schedule goes on
+    // from the parent's lambda there (a decrease is PMF_ERR_NOT_MONOTONE), both
+    // follow lambda on the same side with the same cut rule, and no chain of
+    // forks closes on itself (its instances would all wait)
+    for (int c = 0; c < b->desc.n_inst; ++c) {
+        const int par = b->dinst[c].fork_parent;
+        if (par < 0) continue;
+        const int k = b->dinst[par].fork_k;
+        if (k < 0 || k >= len(par)) return PMF_ERR_INVALID_ARG;
+        if (b->dinst[par].slope_side != b->dinst[c].slope_side || b->dinst[par].cut_rule != b->dinst[c].cut_rule)
+            return PMF_ERR_INVALID_ARG;
+        int a = par, steps = 0;
+        while (a >= 0 && a != c && steps <= b->desc.n_inst) { a = b->dinst[a].fork_parent; ++steps; }
+        if (a == c) return PMF_ERR_INVALID_ARG;
+    }
+    for (int c = 0; c < b->desc.n_inst; ++c) {
+        const int par = b->dinst[c].fork_parent;
+        if (par >= 0 && lambdas[(size_t)c * stride] < lambdas[(size_t)par * stride + b->dinst[par].fork_k])
+            return PMF_ERR_NOT_MONOTONE;
+    }
     DeviceGuard dg(b->device);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (b->in_flight) { cudaEventSynchronize(b->done); b->in_flight = false; }
@@ -641,7 +699,7 @@ static pmf_status solve_impl(pmf_batch *b, const int32_t *lambdas, const int32_t
     b->P.any_sink_side = 0;
     for (int i = 0; i < b->desc.n_inst; ++i) b->P.any_sink_side |= b->dinst[i].slope_side != 0;
     b->P.max_visits_per_tile = b->tune.max_visits_per_tile;
-    const bool geo_changed = (b->P.tile_h != b->tune.tile_h) || len_changed;
+    const bool geo_changed = (b->P.tile_h != b->tune.tile_h) || len_changed || b->forks_changed;
     if (geo_changed) {
         // tile geometry and schedule lengths live in the descriptor table
         for (int i = 0; i < b->desc.n_inst; ++i) b->dinst[i].n_lambda = b->n_lam[i] = len(i);
@@ -926,6 +984,362 @@ void pmf_destroy_batch(pmf_batch *b) {
     pinned_arena().release(b->dinst_h, b->pinned_bytes[4]);
     pinned_arena().release(b->done_h, b->pinned_bytes[5]);
     delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// server mode: one persistent kernel that admits instances while it runs
+// ---------------------------------------------------------------------------
+namespace {
+
+struct ServerLayout {
+    int rows_max, pitch_max;
+    size_t slot_px, max_tiles, max_strips, ring_cap;
+    size_t img_planes, inst_planes, masks, dev_inst, ist, tiles, tile_inst, ring, lambdas, flows, globals,
+        strip_cache, total;
+};
+
+bool server_desc_ok(const pmf_server_desc *d) {
+    return d && d->n_slots >= 1 && d->n_slots <= MB_CAP && d->max_h >= 1 && d->max_w >= 1 &&
+           (int64_t)d->max_h * d->max_w <= (1 << 26) && d->max_lambdas >= 1;
+}
+
+ServerLayout server_layout(const pmf_server_desc *d) {
+    ServerLayout L;
+    L.rows_max = round_up_i(d->max_h, ROW_ALIGN);
+    L.pitch_max = round_up_i(d->max_w, TILE_W);
+    L.slot_px = (size_t)L.rows_max * L.pitch_max;
+    const size_t tx = (size_t)((d->max_w + TILE_IN - 1) / TILE_IN);
+    L.max_tiles = tx * (size_t)(L.rows_max / 4);
+    L.max_strips = tx * (size_t)((L.rows_max + BFS_ROWS - 1) / BFS_ROWS);
+    L.ring_cap = 1;
+    while (L.ring_cap < L.max_tiles * d->n_slots + 16384) L.ring_cap <<= 1;
+    const size_t n = (size_t)d->n_slots;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes); return o; };
+    L.img_planes = take(n * N_IMG_PLANES * L.slot_px * 4);
+    L.inst_planes = take(n * N_INST_PLANES * L.slot_px * 4);
+    L.masks = take(n * (size_t)d->max_lambdas * L.slot_px);
+    L.dev_inst = take(sizeof(DevInst) * n);
+    L.ist = take(sizeof(InstState) * n);
+    L.tiles = take(sizeof(TileState) * n * L.max_tiles);
+    L.tile_inst = take(sizeof(int32_t) * n * L.max_tiles);
+    L.ring = take(sizeof(int32_t) * L.ring_cap);
+    L.lambdas = take(sizeof(int32_t) * n * d->max_lambdas);
+    L.flows = take(sizeof(int64_t) * n * d->max_lambdas);
+    L.globals = take(sizeof(Globals));
+    L.strip_cache = take(sizeof(int32_t) * STRIP_REC_WORDS * n * L.max_strips);
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct pmf_server {
+    pmf_server_desc desc{};
+    ServerLayout L{};
+    char *ws = nullptr;
+    Params P{};
+    pmf_tuning tune{};
+    int n_sm = 0;
+    cudaStream_t kern = nullptr, copy = nullptr;
+    bool running = false;
+    Mailbox *mb = nullptr;                 // mapped host memory
+    int32_t *done_h = nullptr;             // mapped: 1 + status of a slot's finished instance
+    DevInst *dinst_h = nullptr;            // pinned staging of the slots' descriptors
+    int32_t *lam_h = nullptr;              // pinned staging of the slots' schedules
+    char *stage = nullptr;                 // pinned staging of one slot's inputs or results
+    size_t pinned_bytes[5] = {0, 0, 0, 0, 0};
+    std::vector<int> state;                // 0 free, 1 loaded, 2 posted
+    int32_t posted = 0;                    // mailbox entries written
+};
+
+extern "C" {
+
+pmf_status pmf_server_workspace_size(const pmf_server_desc *d, size_t *bytes) {
+    if (!server_desc_ok(d) || !bytes) return PMF_ERR_INVALID_ARG;
+    *bytes = server_layout(d).total;
+    return PMF_OK;
+}
+
+void pmf_server_destroy(pmf_server *s);
+
+pmf_status pmf_server_create(const pmf_server_desc *d, void *dev_workspace, size_t bytes, pmf_server **out) {
+    if (!out) return PMF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!server_desc_ok(d) || !dev_workspace || ((uintptr_t)dev_workspace) % ALIGN) return PMF_ERR_INVALID_ARG;
+    const ServerLayout L = server_layout(d);
+    if (bytes < L.total) return PMF_ERR_OUT_OF_MEMORY;
+    DeviceGuard dg(d->device);
+    pmf_server *s = new (std::nothrow) pmf_server();
+    if (!s) return PMF_ERR_OUT_OF_MEMORY;
+    s->desc = *d;
+    s->L = L;
+    s->ws = (char *)dev_workspace;
+    s->state.assign(d->n_slots, 0);
+    apply_defaults(&s->tune);
+    s->tune.tile_h = 4;
+    s->tune.push_order = 1;
+    cudaError_t e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, d->device);
+    s->pinned_bytes[0] = sizeof(Mailbox);
+    s->pinned_bytes[1] = sizeof(int32_t) * d->n_slots;
+    s->pinned_bytes[2] = sizeof(DevInst) * d->n_slots;
+    s->pinned_bytes[3] = sizeof(int32_t) * (size_t)d->n_slots * d->max_lambdas;
+    // copies to and from pageable memory in the padded layout go row by row;
+    // through pinned staging they are single transfers
+    s->pinned_bytes[4] = std::max(sizeof(int32_t) * 5 * (size_t)d->max_h * d->max_w,
+                                  (size_t)d->max_lambdas * L.slot_px + sizeof(int64_t) * d->max_lambdas);
+    void **dst[5] = {(void **)&s->mb, (void **)&s->done_h, (void **)&s->dinst_h, (void **)&s->lam_h,
+                     (void **)&s->stage};
+    for (int j = 0; j < 5 && e == cudaSuccess; ++j) {
+        *dst[j] = pinned_arena().alloc(s->pinned_bytes[j]);
+        if (!*dst[j]) e = cudaErrorMemoryAllocation;
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->kern, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        pmf_server_destroy(s);
+        return cuda_err_at(e, "pmf_server_create");
+    }
+    std::memset(s->mb, 0, sizeof(Mailbox));
+    std::memset(s->done_h, 0, s->pinned_bytes[1]);
+    Params &P = s->P;
+    P.planes = (int32_t *)(s->ws + L.inst_planes);
+    P.img = (const int32_t *)(s->ws + L.img_planes);
+    P.masks = (uint8_t *)(s->ws + L.masks);
+    P.inst = (const DevInst *)(s->ws + L.dev_inst);
+    P.ist = (InstState *)(s->ws + L.ist);
+    P.tiles = (TileState *)(s->ws + L.tiles);
+    P.tile_inst = (const int32_t *)(s->ws + L.tile_inst);
+    P.ring = (int32_t *)(s->ws + L.ring);
+    P.strip_cache = (int32_t *)(s->ws + L.strip_cache);
+    P.lambdas = (const int32_t *)(s->ws + L.lambdas);
+    P.flows = (long long *)(s->ws + L.flows);
+    P.g = (Globals *)(s->ws + L.globals);
+    P.ring_mask = (unsigned long long)(L.ring_cap - 1);
+    P.n_inst = d->n_slots;
+    P.n_tiles_total = (int32_t)(L.max_tiles * d->n_slots);
+    P.max_lambdas = d->max_lambdas;
+    P.tile_h = 4;
+    P.stall_ns = 5000000000LL;
+    void *dp = nullptr;
+    e = cudaHostGetDevicePointer(&dp, s->mb, 0);
+    P.mailbox = e == cudaSuccess ? (Mailbox *)dp : nullptr;
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dp, s->done_h, 0);
+    P.done_flags = e == cudaSuccess ? (int32_t *)dp : nullptr;
+    if (e != cudaSuccess) {
+        pmf_server_destroy(s);
+        return cuda_err_at(e, "pmf_server_create: mapped memory");
+    }
+    *out = s;
+    return PMF_OK;
+}
+
+pmf_status pmf_server_set_tuning(pmf_server *s, const pmf_tuning *t) {
+    if (!s || !t || s->running) return PMF_ERR_INVALID_ARG;
+    if ((t->tile_h != 0 && t->tile_h != 4) || (t->push_order != 0 && t->push_order != 1) || t->sweeps < 0 ||
+        t->relabel_every < 0 || t->max_visits_per_tile < 0 || t->blocks_per_sm < 0 || t->grid_blocks < 0 ||
+        t->mode != 0)
+        return PMF_ERR_INVALID_ARG;
+    pmf_tuning n = *t;
+    apply_defaults(&n);
+    n.tile_h = 4;
+    n.push_order = 1;
+    s->tune = n;
+    return PMF_OK;
+}
+
+pmf_status pmf_server_start(pmf_server *s, double max_seconds) {
+    if (!s || s->running || !(max_seconds > 0)) return PMF_ERR_INVALID_ARG;
+    DeviceGuard dg(s->desc.device);
+    Params &P = s->P;
+    P.trace = nullptr;
+    P.sweeps = s->tune.sweeps;
+    P.poll_ns = s->tune.poll_ns;
+    P.label_slack = s->tune.label_slack < 0 ? 0 : s->tune.label_slack;
+    P.chain_push = 1;
+    P.relabel_pct = s->tune.relabel_every;
+    P.relabel_extra = s->tune.relabel_extra;
+    P.max_visits_per_tile = s->tune.max_visits_per_tile;
+    P.max_ns = (long long)(max_seconds * 1e9);
+    std::memset(s->mb, 0, sizeof(Mailbox));
+    std::memset(s->done_h, 0, s->pinned_bytes[1]);
+    s->posted = 0;
+    int grid = s->tune.grid_blocks;
+    if (grid <= 0) {
+        int bps = s->tune.blocks_per_sm;
+        if (bps <= 0 && (server_occupancy(&bps) != cudaSuccess || bps <= 0)) bps = 4;
+        grid = bps * s->n_sm;
+    }
+    cudaError_t e = launch_server_reset(P, (int)s->L.max_tiles, s->kern);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->kern);
+    if (e == cudaSuccess) e = launch_server_worker(P, grid, s->kern);
+    if (e != cudaSuccess) return cuda_err_at(e, "pmf_server_start");
+    std::fill(s->state.begin(), s->state.end(), 0);
+    s->running = true;
+    return PMF_OK;
+}
+
+pmf_status pmf_server_load(pmf_server *s, int32_t slot, int32_t image_slot, int32_t H, int32_t W,
+                           const int32_t *w_h, const int32_t *w_v, const int32_t *src0, const int32_t *slope,
+                           const int32_t *sink, const int32_t *lambdas, int32_t n_lambda) {
+    if (!s || slot < 0 || slot >= s->desc.n_slots || image_slot < 0 || image_slot >= s->desc.n_slots)
+        return PMF_ERR_INVALID_ARG;
+    if (H < 1 || W < 1 || H > s->desc.max_h || W > s->desc.max_w || n_lambda < 1 || n_lambda > s->desc.max_lambdas)
+        return PMF_ERR_INVALID_ARG;
+    if (!src0 || !slope || !sink || !lambdas || (image_slot == slot && (!w_h || !w_v))) return PMF_ERR_INVALID_ARG;
+    if (s->state[slot] == 2) return PMF_ERR_NOT_READY;     // posted and not yet read back
+    for (int k = 1; k < n_lambda; ++k)
+        if (lambdas[k] < lambdas[k - 1]) return PMF_ERR_NOT_MONOTONE;
+    DeviceGuard dg(s->desc.device);
+    const ServerLayout &L = s->L;
+    DevInst &d = s->dinst_h[slot];
+    std::memset(&d, 0, sizeof(d));
+    d.H = H;
+    d.W = W;
+    d.rows = round_up_i(H, ROW_ALIGN);
+    d.pitch = round_up_i(W, TILE_W);
+    d.image = image_slot;
+    d.tiles_x = (W + TILE_IN - 1) / TILE_IN;
+    d.tiles_y = d.rows / 4;
+    d.n_tiles = d.tiles_x * d.tiles_y;
+    d.tile_base = (int32_t)(L.max_tiles * slot);
+    d.n_lambda = n_lambda;
+    d.hcap = H * W + 1;
+    d.lead_base = (int32_t)(L.max_strips * slot);
+    d.plane_off = (int64_t)((size_t)slot * N_INST_PLANES * L.slot_px);
+    d.img_off = (int64_t)((size_t)image_slot * N_IMG_PLANES * L.slot_px);
+    d.mask_off = (int64_t)((size_t)slot * s->desc.max_lambdas * L.slot_px);
+    d.n_leads = d.tiles_x * ((d.tiles_y + BFS_ROWS / 4 - 1) / (BFS_ROWS / 4));
+    d.fork_parent = d.fork_child = d.fork_k = -1;
+    int32_t *lrow = s->lam_h + (size_t)slot * s->desc.max_lambdas;
+    for (int k = 0; k < s->desc.max_lambdas; ++k) lrow[k] = lambdas[std::min(k, n_lambda - 1)];
+    const size_t ps = (size_t)d.rows * d.pitch;
+    cudaStream_t c = s->copy;
+    // the inputs in the padded layout (rows x pitch), through pinned staging;
+    // the kernel's set-up pass zeroes the padding and checks every value
+    const size_t n = (size_t)H * W;
+    int32_t *stg = (int32_t *)s->stage;
+    const bool own_image = image_slot == slot;
+    std::memcpy(stg, src0, n * 4);
+    std::memcpy(stg + n, slope, n * 4);
+    std::memcpy(stg + 2 * n, sink, n * 4);
+    if (own_image) {
+        std::memcpy(stg + 3 * n, w_h, n * 4);
+        std::memcpy(stg + 4 * n, w_v, n * 4);
+    }
+    auto put = [&](char *dst_, const int32_t *src) {
+        return cudaMemcpy2DAsync(dst_, (size_t)d.pitch * 4, src, (size_t)W * 4, (size_t)W * 4, H,
+                                 cudaMemcpyHostToDevice, c);
+    };
+    char *ip = s->ws + L.inst_planes + (size_t)d.plane_off * 4;
+    cudaError_t e = put(ip + (size_t)P_SRC0 * ps * 4, stg);
+    if (e == cudaSuccess) e = put(ip + (size_t)P_SLOPE * ps * 4, stg + n);
+    if (e == cudaSuccess) e = put(ip + (size_t)P_CT * ps * 4, stg + 2 * n);
+    if (e == cudaSuccess && own_image) {
+        char *im = s->ws + L.img_planes + (size_t)d.img_off * 4;
+        e = put(im, stg + 3 * n);
+        if (e == cudaSuccess) e = put(im + ps * 4, stg + 4 * n);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->ws + L.lambdas + sizeof(int32_t) * (size_t)slot * s->desc.max_lambdas, lrow,
+                            sizeof(int32_t) * s->desc.max_lambdas, cudaMemcpyHostToDevice, c);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->ws + L.dev_inst + sizeof(DevInst) * slot, &d, sizeof(DevInst), cudaMemcpyHostToDevice, c);
+    // the staging buffer is reused by the next call
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c);
+    if (e != cudaSuccess) return cuda_err_at(e, "pmf_server_load");
+    s->state[slot] = 1;
+    return PMF_OK;
+}
+
+pmf_status pmf_server_post(pmf_server *s, const int32_t *slots, int32_t n) {
+    if (!s || !slots || n < 1 || !s->running) return PMF_ERR_INVALID_ARG;
+    for (int j = 0; j < n; ++j)
+        if (slots[j] < 0 || slots[j] >= s->desc.n_slots || s->state[slots[j]] != 1) return PMF_ERR_INVALID_ARG;
+    DeviceGuard dg(s->desc.device);
+    // the slots' inputs are in device memory before the kernel may read them
+    const cudaError_t e = cudaStreamSynchronize(s->copy);
+    if (e != cudaSuccess) return cuda_err_at(e, "pmf_server_post");
+    for (int j = 0; j < n; ++j) {
+        const int slot = slots[j];
+        *(volatile int32_t *)(s->done_h + slot) = 0;
+        s->mb->ring[(s->posted + j) % MB_CAP] = slot;
+        s->state[slot] = 2;
+    }
+    s->posted += n;
+    std::atomic_thread_fence(std::memory_order_seq_cst);      // entries before the tail
+    *(volatile int32_t *)&s->mb->tail = s->posted;
+    return PMF_OK;
+}
+
+pmf_status pmf_server_poll(pmf_server *s, uint8_t *done, int32_t *n_done) {
+    if (!s) return PMF_ERR_INVALID_ARG;
+    int n = 0;
+    for (int i = 0; i < s->desc.n_slots; ++i) {
+        const bool d = s->state[i] == 2 && *(volatile int32_t *)(s->done_h + i) != 0;
+        if (done) done[i] = d ? 1 : 0;
+        n += d;
+    }
+    if (n_done) *n_done = n;
+    return PMF_OK;
+}
+
+pmf_status pmf_server_read(pmf_server *s, int32_t slot, uint8_t *masks, int64_t *flows) {
+    if (!s || slot < 0 || slot >= s->desc.n_slots || !masks || !flows) return PMF_ERR_INVALID_ARG;
+    if (s->state[slot] != 2) return PMF_ERR_NOT_READY;
+    const int f = *(volatile int32_t *)(s->done_h + slot);
+    if (f == 0) return PMF_ERR_NOT_READY;
+    s->state[slot] = 0;                                     // the slot may be loaded again
+    const pmf_status st = (pmf_status)(f - 1);
+    if (st != PMF_OK) return st;
+    DeviceGuard dg(s->desc.device);
+    const DevInst &d = s->dinst_h[slot];
+    // the slot's masks as stored (n_lambda x rows x pitch) and its flows in one
+    // pinned transfer each, then the padding dropped on the host
+    const size_t ps = (size_t)d.rows * d.pitch;
+    char *stg = s->stage;
+    int64_t *fstg = (int64_t *)(stg + (size_t)s->desc.max_lambdas * s->L.slot_px);
+    cudaError_t e = cudaMemcpyAsync(stg, s->ws + s->L.masks + d.mask_off, ps * d.n_lambda, cudaMemcpyDeviceToHost,
+                                    s->copy);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(fstg, s->ws + s->L.flows + sizeof(int64_t) * (size_t)slot * s->desc.max_lambdas,
+                            sizeof(int64_t) * d.n_lambda, cudaMemcpyDeviceToHost, s->copy);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy);
+    if (e != cudaSuccess) return cuda_err_at(e, "pmf_server_read");
+    for (int k = 0; k < d.n_lambda; ++k)
+        for (int y = 0; y < d.H; ++y)
+            std::memcpy(masks + ((size_t)k * d.H + y) * d.W, stg + (size_t)k * ps + (size_t)y * d.pitch, d.W);
+    std::memcpy(flows, fstg, sizeof(int64_t) * d.n_lambda);
+    return PMF_OK;
+}
+
+pmf_status pmf_server_stop(pmf_server *s) {
+    if (!s || !s->running) return PMF_ERR_INVALID_ARG;
+    DeviceGuard dg(s->desc.device);
+    *(volatile int32_t *)&s->mb->stop = 1;
+    cudaError_t e = cudaStreamSynchronize(s->kern);
+    s->running = false;
+    if (e != cudaSuccess) return cuda_err_at(e, "pmf_server_stop");
+    Globals g;
+    e = cudaMemcpy(&g, s->ws + s->L.globals, sizeof(Globals), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err_at(e, "pmf_server_stop: read state");
+    return g.err ? PMF_ERR_NOT_CONVERGED : PMF_OK;
+}
+
+void pmf_server_destroy(pmf_server *s) {
+    if (!s) return;
+    DeviceGuard dg(s->desc.device);
+    if (s->running) (void)pmf_server_stop(s);
+    if (s->kern) cudaStreamDestroy(s->kern);
+    if (s->copy) cudaStreamDestroy(s->copy);
+    pinned_arena().release(s->mb, s->pinned_bytes[0]);
+    pinned_arena().release(s->done_h, s->pinned_bytes[1]);
+    pinned_arena().release(s->dinst_h, s->pinned_bytes[2]);
+    pinned_arena().release(s->lam_h, s->pinned_bytes[3]);
+    pinned_arena().release(s->stage, s->pinned_bytes[4]);
+    delete s;
 }
 
 }  // extern "C"

@@ -30,7 +30,14 @@ enum Plane { P_E = 0, P_H = 1, P_RT = 2, P_FR = 3, P_FD = 4, P_SRC0 = 5, P_SLOPE
 // the pass that finds the pixels reachable from excess (its cut)
 // PH_WARM: at the start of each later lambda step, the strip pass that raises
 // the source capacities (GGT warm start) and counts the tiles left active
-enum Phase { PH_BFS = 0, PH_PR = 1, PH_DONE = 2, PH_FWD = 3, PH_WARM = 4 };
+// PH_COPY: after the certified step an instance forks at, the strip pass that
+// copies its state into the forked instance (pmf_set_fork)
+// PH_WAIT: a forked instance before its parent's copy pass has run
+// PH_SETUP: server mode, a newly admitted instance's strip pass: it checks its
+// capacities, zeroes the padding, sets up the lambda_0 preflow and resets its
+// tiles; then the first global relabel
+enum Phase { PH_BFS = 0, PH_PR = 1, PH_DONE = 2, PH_FWD = 3, PH_WARM = 4, PH_COPY = 5, PH_WAIT = 6,
+             PH_SETUP = 7 };
 // tile queue states
 enum TState { T_IDLE = 0, T_QUEUED = 1, T_RUNNING = 2, T_DIRTY = 3 };
 // global error flags; GE_INTERNAL_MASK marks a broken scheduler invariant, after
@@ -54,7 +61,11 @@ struct DevInst {                 // read-only during a solve
     int32_t n_leads;             // relabel strips (tiles_x * ceil(tiles_y / strip_span))
     int16_t cut_rule;            // 0: maximal source set; 1: s and t swapped by the caller (pmf_set_cut_rule)
     int16_t slope_side;          // 0: cs = src0 + slope*lambda, ct = sink; 1: cs = src0, ct = sink - slope*lambda
+    int32_t fork_parent;         // -1, or the instance whose state this one starts from (pmf_set_fork)
+    int32_t fork_child;          // -1, or the instance forked from this one
+    int32_t fork_k;              // the step of this instance after which its child is forked
 };
+static_assert(sizeof(DevInst) % 16 == 0, "DevInst is loaded as int4s");
 
 // 16-byte aligned: the worker reads the first four fields with one 16-byte
 // vector load, which faults on a misaligned address
@@ -69,7 +80,8 @@ struct alignas(128) InstState {  // mutable during a solve
     unsigned long long pr_mark;      // pr_visits when the current push/relabel phase began
     unsigned long long step_mark;    // pr_visits + bfs_visits when the current lambda step began
     unsigned long long epochs;       // global relabels so far
-    int32_t pad_b_, pad_c_;
+    int32_t lam_prev;                // lambda the state was certified at (the warm start raises from it)
+    int32_t pad_c_;
     // updated atomically by the workers, on their own cache line
     alignas(128) int32_t outstanding, active, dmax, pad3_;
     unsigned long long flow;         // int64 two's complement: total flow into t
@@ -108,6 +120,9 @@ struct Globals {
     unsigned long long t_start;      // %globaltimer at the start of the launch
     unsigned long long progress;     // bumped by warps running kept items (no queue traffic)
     alignas(128) unsigned long long trace_n;
+    // server mode: mailbox entries taken, instances started, next mailbox check
+    alignas(128) int32_t cmd_head, admitted;
+    unsigned long long mb_next_ns;
     // warp-time breakdown (ns summed over warps), recorded with the trace:
     // [0] waiting for work, [1] push/relabel visits, [2] relabel (BFS) visits,
     // [3] retiring items (wake-ups, requeue, phase changes), [4] sweeps run,
@@ -117,8 +132,19 @@ struct Globals {
     unsigned long long prof[PMF_PROFILE_COUNTERS];
 };
 
+// Server mode: the host posts instance slots whose inputs it has copied in
+// to a mailbox in mapped host memory; idle workers take them from there.
+constexpr int MB_CAP = 4096;
+struct Mailbox {
+    int32_t tail;                // entries posted so far (written by the host after the entry)
+    int32_t stop;                // 1: the kernel ends once every posted instance is finished
+    int32_t pad_[30];
+    int32_t ring[MB_CAP];        // slot of entry t at ring[t % MB_CAP]
+};
+
 struct Params {
     TraceEvent *trace;           // phase-change trace (TRACE_CAP records) or nullptr
+    Mailbox *mailbox;            // server mode (device address of mapped host memory), else nullptr
     int32_t *planes;             // instance planes base
     const int32_t *img;          // image planes base
     uint8_t *masks;
@@ -137,6 +163,8 @@ struct Params {
     unsigned long long ring_mask;
     int32_t n_inst, n_tiles_total, max_lambdas, sweeps;
     int32_t n_leads_total, chain_push;   // chain_push: push order of the sweeps (pmf_tuning.push_order)
+    int32_t n_leads_queued;      // relabel strips queued at the start (forked instances' strips come last
+                                 // and wait for their parent)
     int32_t relabel_pct, tile_h;
     int32_t relabel_extra;       // visits added to every phase's budget
     int32_t any_sink_side;       // some instance's sink capacities fall with lambda (slope_side 1)
@@ -154,6 +182,10 @@ cudaError_t launch_pad_terminals(const Params &P, int inst, const DevInst &d, co
 cudaError_t launch_reset(const Params &P, cudaStream_t s);
 cudaError_t launch_init(const Params &P, int max_pixels, cudaStream_t s);
 cudaError_t launch_worker(const Params &P, int grid, cudaStream_t s);
+// server mode: clear the slots' tiles, queue and instance states (slot = tile / max_tiles)
+cudaError_t launch_server_reset(const Params &P, int max_tiles, cudaStream_t s);
+cudaError_t launch_server_worker(const Params &P, int grid, cudaStream_t s);
+cudaError_t server_occupancy(int *blocks_per_sm);
 cudaError_t launch_begin_round(const Params &P, cudaStream_t s);
 cudaError_t launch_return_excess(const Params &P, const DevInst &d, int lambda, int max_sweeps,
                                  int32_t *f_h, int32_t *f_v, int32_t *f_s, int32_t *f_t, int32_t *status,

@@ -62,6 +62,15 @@ __device__ __forceinline__ unsigned long long ldv64(const unsigned long long *p)
     return *(const volatile unsigned long long *)p;
 }
 __device__ __forceinline__ long long ldv64s(const long long *p) { return *(const volatile long long *)p; }
+// a load of data that stays fixed while a batch solves (descriptors, lambda
+// table, capacity planes): through the non-coherent read-only path in batch
+// kernels; through L2 in the server kernel (SV), where the host rewrites a
+// slot's data between the requests that occupy it
+template <bool SV, typename T>
+__device__ __forceinline__ T ldro(const T *p) {
+    if constexpr (SV) return __ldcg(p);
+    else return __ldg(p);
+}
 
 // per-warp scratch: values of the two border columns at load (their updates
 // are written back as deltas)
@@ -170,13 +179,14 @@ __device__ int ring_pop_round(const Params &P) {   // one lane; -1 = round over
 
 // read-only instance descriptor through the non-coherent (texture) path; the
 // table is written before the worker launch and never during it
+template <bool SV>
 __device__ __forceinline__ DevInst load_inst(const Params &P, int inst) {
     static_assert(sizeof(DevInst) % 16 == 0, "DevInst is loaded as int4s");
     DevInst d;
     const int4 *src = reinterpret_cast<const int4 *>(P.inst + inst);
     int4 *dst = reinterpret_cast<int4 *>(&d);
 #pragma unroll
-    for (int j = 0; j < (int)(sizeof(DevInst) / 16); ++j) dst[j] = __ldg(src + j);
+    for (int j = 0; j < (int)(sizeof(DevInst) / 16); ++j) dst[j] = ldro<SV>(src + j);
     return d;
 }
 
@@ -281,21 +291,86 @@ __device__ void mark_done(const Params &P, int inst, int status) {
     if (P.done_flags) *(volatile int32_t *)(P.done_flags + inst) = 1 + status;
 }
 
+// A forked instance whose parent stopped before forking it never starts:
+// it and every instance forked from it finish with the parent's status.
+template <bool SV>
+__device__ __noinline__ void cancel_forks(const Params &P, int child, int status) {
+    for (int c = child, it = 0; c >= 0 && it < P.n_inst; ++it) {
+        volatile InstState *C = P.ist + c;
+        if (C->phase != PH_WAIT) break;
+        C->status = status;
+        C->phase = PH_DONE;
+        atomicAdd(&P.g->inst_done, 1);
+        mark_done(P, c, status);
+        c = ldro<SV>(&P.inst[c].fork_child);
+    }
+}
+
+// Start a forked instance once its parent's copy pass has written the
+// parent's state into its planes: it continues from the parent's lambda
+// (flow value, largest distance and labels as the parent certified them) with
+// the warm-start pass of its own first lambda.  Returns true when the child's
+// strips all finished before the guard was released: the caller must then run
+// the child's next phase change.
+template <bool SV>
+__device__ __noinline__ bool start_fork(const Params &P, int child, volatile InstState *parent) {
+    const int lane = threadIdx.x & 31;
+    volatile InstState *C = P.ist + child;
+    const DevInst DC = load_inst<SV>(P, child);
+    int go = 0;
+    if (lane == 0) {
+        if (C->status != PMF_OK) {
+            const int st = C->status;
+            C->phase = PH_WAIT;             // cancel_forks finishes it with its own status
+            cancel_forks<SV>(P, child, st);
+        } else {
+            C->flow = parent->flow;
+            C->dmax = parent->dmax;
+            C->lam_prev = parent->lam_prev;
+            C->k = 0;
+            C->want_bfs = 0;
+            C->step_mark = 0;
+            C->phase = PH_WARM;
+            go = 1;
+            atomicAdd(&P.ist[child].outstanding, 1);   // guard while its strips are queued
+        }
+        __threadfence();
+    }
+    go = __shfl_sync(FULL_MASK, go, 0);
+    if (!go) return false;
+    __syncwarp();
+    enqueue_tiles(P, child, DC, false, true);
+    int last = 0;
+    if (lane == 0) {
+        __threadfence();
+        last = atomicAdd(&P.ist[child].outstanding, -1) == 1;
+    }
+    return __shfl_sync(FULL_MASK, last, 0) != 0;
+}
+
 // One phase change.  Returns true when the items it queued had all finished
 // before it let go of its guard: the caller is then the instance's last
-// finisher again and must run the next phase change itself.
-__device__ bool transition_once(const Params &P, int inst) {
+// finisher again and must run the next phase change itself.  *other is set to
+// an instance (a child it forked) whose own phase change the caller must run.
+template <bool SV>
+__device__ bool transition_once(const Params &P, int inst, int *other) {
     const int lane = threadIdx.x & 31;
     volatile InstState *S = P.ist + inst;
-    const DevInst D = load_inst(P, inst);
+    const DevInst D = load_inst<SV>(P, inst);
     __threadfence();
     int mode = 0;   // 0 nothing, 1 all tiles, 2 tiles with active pixels
+    int fork_now = 0;
     if (lane == 0) {
         const int phase = S->phase;
         if (S->status != PMF_OK) {
             S->phase = PH_DONE;
             atomicAdd(&P.g->inst_done, 1);
             mark_done(P, inst, S->status);
+            cancel_forks<SV>(P, D.fork_child, S->status);
+        } else if (phase == PH_SETUP) {        // server: set up, start the first global relabel
+            S->dmax = 0;
+            S->phase = PH_BFS;
+            mode = 1;
         } else if (phase == PH_WARM) {         // the step's first push/relabel phase
             S->phase = PH_PR;
             S->pr_mark = S->pr_visits;
@@ -317,15 +392,32 @@ __device__ bool transition_once(const Params &P, int inst) {
             S->epoch = S->epoch + 1;
             S->phase = PH_FWD;
             mode = 1;
+        } else if (phase == PH_COPY) {
+            // the copy pass is over: start the child, then go on
+            fork_now = 1;
+            if (S->k >= D.n_lambda) {
+                S->phase = PH_DONE;
+                atomicAdd(&P.g->inst_done, 1);
+                mark_done(P, inst, PMF_OK);
+                trace(P, inst, TR_DONE, S);
+            } else {
+                S->phase = PH_WARM;
+                mode = 1;
+            }
         } else if (phase == PH_BFS || phase == PH_FWD) {
             const unsigned long long visits = S->pr_visits + S->bfs_visits;
             if (phase == PH_FWD || S->active == 0) {   // lambda step certified: record, advance
                 const int k = S->k;
                 if (phase == PH_BFS) P.flows[(size_t)inst * P.max_lambdas + k] = (long long)S->flow;
                 S->k = k + 1;
+                S->lam_prev = ldro<SV>(P.lambdas + (size_t)inst * P.max_lambdas + k);
                 S->step_mark = visits;
                 trace(P, inst, TR_STEP_DONE, S);
-                if (k + 1 >= D.n_lambda) {
+                if (D.fork_child >= 0 && k == D.fork_k) {
+                    // copy this state into the forked instance, strip by strip
+                    S->phase = PH_COPY;
+                    mode = 1;
+                } else if (k + 1 >= D.n_lambda) {
                     S->phase = PH_DONE;
                     atomicAdd(&P.g->inst_done, 1);
                     mark_done(P, inst, PMF_OK);
@@ -341,6 +433,7 @@ __device__ bool transition_once(const Params &P, int inst) {
                 atomicAdd(&P.g->inst_done, 1);
                 mark_done(P, inst, PMF_ERR_NOT_CONVERGED);
                 trace(P, inst, TR_NOT_CONVERGED, S);
+                cancel_forks<SV>(P, D.fork_child, PMF_ERR_NOT_CONVERGED);
             } else {
                 S->phase = PH_PR;
                 S->pr_mark = S->pr_visits;
@@ -352,6 +445,8 @@ __device__ bool transition_once(const Params &P, int inst) {
         __threadfence();
     }
     mode = __shfl_sync(FULL_MASK, mode, 0);
+    fork_now = __shfl_sync(FULL_MASK, fork_now, 0);
+    if (fork_now && start_fork<SV>(P, D.fork_child, S)) *other = D.fork_child;
     if (!mode) return false;
     // the phase's parameters are published before any of its tiles can run
     const int n = (mode == 2) ? count_active_tiles(P, D) : D.n_tiles;
@@ -375,9 +470,11 @@ __device__ bool transition_once(const Params &P, int inst) {
     if (lane == 0) atomicAdd(&P.ist[inst].outstanding, 1);
     __threadfence();
     __syncwarp();
-    // a relabel or forward pass works on strips (their leader tiles are
-    // queued); push/relabel on tiles
-    enqueue_tiles(P, inst, D, mode == 2, S->phase == PH_BFS || S->phase == PH_FWD || S->phase == PH_WARM);
+    // a relabel, forward, warm-start or copy pass works on strips (their
+    // leader tiles are queued); push/relabel on tiles
+    const int ph = S->phase;
+    enqueue_tiles(P, inst, D, mode == 2,
+                  ph == PH_BFS || ph == PH_FWD || ph == PH_WARM || ph == PH_COPY || ph == PH_SETUP);
     int last = 0;
     if (lane == 0) {
         __threadfence();
@@ -390,10 +487,20 @@ __device__ bool transition_once(const Params &P, int inst) {
 // outstanding item.  Repeats while a phase ends before its own queueing did
 // (a phase with no tiles to queue, or tiles that all finished meanwhile);
 // every repetition is a phase change that the visit watchdog counts, and a
-// hard cap flags the launch if it is ever reached.
+// hard cap flags the launch if it is ever reached.  A forked child whose
+// strips all finished before its start was complete is run the same way.
+template <bool SV>
 __device__ void transition(const Params &P, int inst) {
-    for (int it = 0; it < (1 << 16); ++it)
-        if (!transition_once(P, inst)) return;
+    int cur = inst, pending = -1;
+    for (int it = 0; it < (1 << 16); ++it) {
+        int other = -1;
+        const bool again = transition_once<SV>(P, cur, &other);
+        if (other >= 0) pending = other;
+        if (again) continue;
+        if (pending < 0) return;
+        cur = pending;
+        pending = -1;
+    }
     if ((threadIdx.x & 31) == 0) atomicOr(&P.g->err, GE_RING);
 }
 
@@ -406,6 +513,7 @@ __device__ void transition(const Params &P, int inst) {
 // warp instead of queueing it: chains of dependent visits then stay on an SM
 // whose caches hold the code and the neighbourhood (the queue otherwise hands
 // an item to the warp that has been idle longest).  Returns -1 otherwise.
+template <bool SV>
 __device__ int finish(const Params &P, int g, int inst, int phase, bool requeue, unsigned nb,
                       const DevInst &D, bool keep) {
     const int lane = threadIdx.x & 31;
@@ -481,7 +589,7 @@ __device__ int finish(const Params &P, int g, int inst, int phase, bool requeue,
         int dummy;
         if (slot_wait(P, slot, true, &dummy)) *slot = item;
     }
-    if (trans) transition(P, inst);      // only when k == 0, so nothing is kept
+    if (trans) transition<SV>(P, inst);  // only when k == 0, so nothing is kept
     return kept;
 }
 
@@ -518,7 +626,7 @@ __device__ __forceinline__ TileGeo tile_geo(int g, const DevInst &D, int TH) {
 // push/relabel visit of one tile (Goldberg-Tarjan push and relabel operations,
 // the solver the paper runs through NPPI, Section 3)
 // --------------------------------------------------------------------------
-template <int TH, int PO>
+template <int TH, int PO, bool SV>
 __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, const DevInst &D,
                          int kcur, bool &self_active, unsigned &nbmask) {
     const TileGeo T = tile_geo(g, D, TH);
@@ -543,8 +651,8 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
         rt[i] = own ? __ldcg(RT + idx) : 0;
         fr[i] = (T.inb && lane != 31) ? __ldcg(FR + idx) : 0;
         fd[i] = own ? __ldcg(FD + idx) : 0;
-        wh[i] = (T.inb && lane != 31) ? __ldg(WH + idx) : 0;
-        wv[i] = own ? __ldg(WV + idx) : 0;
+        wh[i] = (T.inb && lane != 31) ? ldro<SV>(WH + idx) : 0;
+        wv[i] = own ? ldro<SV>(WV + idx) : 0;
         srt0 += rt[i];
     }
     const int e0top = e[0], e0bot = e[TH - 1], fd0b = fd[TH - 1];
@@ -564,7 +672,7 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
     if (own && T.y0 > 0) {
         const size_t j = (size_t)(T.y0 - 1) * pitch + T.X;
         hT = __ldcg(Hh + j);
-        wvT = __ldg(WV + j);
+        wvT = ldro<SV>(WV + j);
         fdT = __ldcg(FD + j);
     }
     const int fdT0 = fdT;
@@ -861,7 +969,7 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
 // the step's first push/relabel phase.  Nothing else of the instance runs in
 // this phase, so every value is written directly.
 // --------------------------------------------------------------------------
-template <int TH, bool SINK>
+template <int TH, bool SINK, bool SV>
 __device__ void warm_visit(const Params &P, int g, int inst, const DevInst &D, int kcur) {
     constexpr int BR = BFS_ROWS;
     constexpr int SPAN = BR / TH;
@@ -874,10 +982,12 @@ __device__ void warm_visit(const Params &P, int g, int inst, const DevInst &D, i
     int *E = base + P_E * PS, *RT = base + P_RT * PS;
     const int *Hh = base + P_H * PS, *SLOPE = base + P_SLOPE * PS;
     const int *L = P.lambdas + (size_t)inst * P.max_lambdas;
-    const int dl = __ldg(L + kcur) - __ldg(L + kcur - 1);
+    // from the lambda the state was certified at: the previous step's, or for
+    // a forked instance's first step its parent's
+    const int dl = ldro<SV>(L + kcur) - ldv(&P.ist[inst].lam_prev);
     // which terminal arcs follow lambda (only kernels built for batches with
     // falling sink capacities look)
-    const bool sink_side = SINK && __ldg(&P.inst[inst].slope_side) != 0;
+    const bool sink_side = SINK && ldro<SV>(&P.inst[inst].slope_side) != 0;
     // the member tiles' counts as last written, kept in the strip record
     int32_t *cnt_rec = P.strip_cache + (size_t)(D.lead_base + (T.ty / SPAN) * D.tiles_x + T.tx) * STRIP_REC_WORDS
                        + RW_CNT * 32;
@@ -896,7 +1006,7 @@ __device__ void warm_visit(const Params &P, int g, int inst, const DevInst &D, i
             e[j] = ok ? __ldcg(E + idx) : 0;
             rt[j] = ok ? __ldcg(RT + idx) : 0;
             h[j] = ok ? __ldcg(Hh + idx) : HINF;
-            sl[j] = ok ? __ldg(SLOPE + idx) : 0;
+            sl[j] = ok ? ldro<SV>(SLOPE + idx) : 0;
         }
 #pragma unroll
         for (int j = 0; j < LB; ++j) {
@@ -963,6 +1073,45 @@ __device__ void warm_visit(const Params &P, int g, int inst, const DevInst &D, i
 }
 
 // --------------------------------------------------------------------------
+// copy visit: one strip of a parent's state (e, h, rt, fR, fD and the terminal
+// planes src0, slope, ct) into the instance forked from it.  Both instances
+// have the same image, so the same layout; nothing of either runs meanwhile
+// (the parent is in its copy pass, the child waits for it).
+// --------------------------------------------------------------------------
+template <int TH, bool SV>
+__device__ __noinline__ void copy_visit(const Params &P, int g, int inst, const DevInst &D) {
+    constexpr int BR = BFS_ROWS;
+    const TileGeo T = tile_geo(g, D, TH);
+    const bool own = T.inb && !T.ghost;
+    const int pitch = D.pitch;
+    const size_t PS = (size_t)D.rows * pitch;
+    const int *src = P.planes + D.plane_off;
+    int *dst = P.planes + ldro<SV>(&P.inst[D.fork_child].plane_off);
+    constexpr int LB = 4;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BR; c0 += LB) {
+        int v[LB][N_INST_PLANES];
+#pragma unroll
+        for (int j = 0; j < LB; ++j) {
+            const int y = T.y0 + c0 + j;
+            const bool ok = own && y < D.rows;
+            const size_t idx = (size_t)y * pitch + T.X;
+#pragma unroll
+            for (int q = 0; q < N_INST_PLANES; ++q) v[j][q] = ok ? __ldcg(src + q * PS + idx) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < LB; ++j) {
+            const int y = T.y0 + c0 + j;
+            if (own && y < D.rows) {
+                const size_t idx = (size_t)y * pitch + T.X;
+#pragma unroll
+                for (int q = 0; q < N_INST_PLANES; ++q) __stcg(dst + q * PS + idx, v[j][q]);
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
 // global-relabel visit: one strip's share of the BFS from t over reverse
 // residual arcs (exact distances by label-correcting relaxation to a fixpoint;
 // unreachable pixels keep HINF).  A strip is a column of BFS_ROWS / TH tiles
@@ -972,7 +1121,7 @@ __device__ void warm_visit(const Params &P, int g, int inst, const DevInst &D, i
 // the current lambda (1 = cannot reach t = source side) and each member tile's
 // count of active pixels for the push/relabel phase that may follow.
 // --------------------------------------------------------------------------
-template <int TH, bool FWD>
+template <int TH, bool FWD, bool SV>
 __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, const DevInst &D,
                           int epoch, int kcur, bool &self_again, unsigned &nbmask) {
     constexpr int BR = BFS_ROWS;
@@ -1082,7 +1231,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     // the row above the strip: residual of the arcs up and down across the border
     if (own && T.y0 > 0) {
         const size_t j = (size_t)(T.y0 - 1) * pitch + T.X;
-        const int wvT = __ldg(WV + j), fdT = __ldcg(FD + j);
+        const int wvT = ldro<SV>(WV + j), fdT = __ldcg(FD + j);
         res_up0 = wvT + fdT;          // row 0 -> above
         res_down_above = wvT - fdT;   // above -> row 0
         if (vT) {
@@ -1112,9 +1261,9 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
             const bool ldc = T.inb && rowok && lane != 31;
             const bool ldo = own && rowok;
             fr[j] = ldc ? __ldcg(FR + idx) : 0;
-            wh[j] = ldc ? __ldg(WH + idx) : 0;
+            wh[j] = ldc ? ldro<SV>(WH + idx) : 0;
             fd[j] = ldo ? __ldcg(FD + idx) : 0;
-            wv[j] = ldo ? __ldg(WV + idx) : 0;
+            wv[j] = ldo ? ldro<SV>(WV + idx) : 0;
             rt[j] = ldo ? __ldcg(RT + idx) : 0;
             ev[j] = ldo ? __ldcg(E + idx) : 0;
             if constexpr (FWD) dv[j] = (T.inb && rowok && vX) ? ghost_label(c0 + j) : HINF;
@@ -1340,15 +1489,207 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
 }
 
 // --------------------------------------------------------------------------
+// server mode: admission of posted instances into the running kernel
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int flags_status(int f) {
+    if (f & VF_SLOPE) return PMF_ERR_NOT_MONOTONE;
+    if (f & VF_OVERFLOW) return PMF_ERR_OVERFLOW;
+    if (f & VF_NEG) return PMF_ERR_INVALID_ARG;
+    return PMF_OK;
+}
+
+// Set-up visit of one strip of a newly admitted instance (its capacities were
+// copied in by the host, row-major with the padded pitch): padding and the
+// ignored last column of w_h / last row of w_v become zero, capacities are
+// checked, the lambda_0 preflow is set up (as init_kernel does for a batch)
+// and the member tiles and the strip record start afresh.
+template <int TH>
+__device__ void setup_visit(const Params &P, int g, int inst, const DevInst &D) {
+    constexpr int BR = BFS_ROWS;
+    constexpr int SPAN = BR / TH;
+    const TileGeo T = tile_geo(g, D, TH);
+    const int lane = T.lane;
+    const bool own = T.inb && !T.ghost;
+    const int pitch = D.pitch;
+    const size_t PS = (size_t)D.rows * pitch;
+    int *base = P.planes + D.plane_off;
+    int *WH = const_cast<int *>(P.img) + D.img_off, *WV = WH + PS;
+    const int *L = P.lambdas + (size_t)inst * P.max_lambdas;
+    const long long lam0 = __ldcg(L), lamN = __ldcg(L + D.n_lambda - 1);
+    long long fsum = 0;
+    int bad = 0;
+#pragma unroll 1
+    for (int i = 0; i < BR; ++i) {
+        const int y = T.y0 + i;
+        if (!own || y >= D.rows) continue;
+        const size_t idx = (size_t)y * pitch + T.X;
+        const bool in = y < D.H && T.X < D.W;
+        const int wh = (in && T.X < D.W - 1) ? __ldcg(WH + idx) : 0;
+        const int wv = (in && y < D.H - 1) ? __ldcg(WV + idx) : 0;
+        const int s0 = in ? __ldcg(base + P_SRC0 * PS + idx) : 0;
+        const int sl = in ? __ldcg(base + P_SLOPE * PS + idx) : 0;
+        const int ct = in ? __ldcg(base + P_CT * PS + idx) : 0;
+        if (wh < 0 || wv < 0 || s0 < 0 || ct < 0) bad |= VF_NEG;
+        if (wh > PMF_MAX_PAIRWISE || wv > PMF_MAX_PAIRWISE || s0 > PMF_INF || ct > PMF_INF) bad |= VF_OVERFLOW;
+        if (sl < 0) bad |= VF_SLOPE;
+        const long long cs0 = (long long)s0 + (long long)sl * lam0, csN = (long long)s0 + (long long)sl * lamN;
+        if (csN > PMF_INF) bad |= VF_OVERFLOW;
+        const bool ok = s0 >= 0 && ct >= 0 && sl >= 0 && csN <= PMF_INF;
+        if (!in || T.X >= D.W - 1) __stcg(WH + idx, 0);
+        if (!in || y >= D.H - 1) __stcg(WV + idx, 0);
+        if (!in) {
+            __stcg(base + P_SRC0 * PS + idx, 0);
+            __stcg(base + P_SLOPE * PS + idx, 0);
+            __stcg(base + P_CT * PS + idx, 0);
+        }
+        int e = ok ? (int)cs0 : 0, rt = ok ? ct : 0;
+        const int m = min(e, rt);
+        e -= m;
+        rt -= m;
+        fsum += m;
+        __stcg(base + P_E * PS + idx, e);
+        __stcg(base + P_RT * PS + idx, rt);
+        __stcg(base + P_H * PS + idx, HINF);
+        __stcg(base + P_FR * PS + idx, 0);
+        __stcg(base + P_FD * PS + idx, 0);
+    }
+    // the member tiles and the strip record start from zero counts and epochs
+    int32_t *cnt = P.strip_cache + (size_t)(D.lead_base + (T.ty / SPAN) * D.tiles_x + T.tx) * STRIP_REC_WORDS +
+                   RW_CNT * 32;
+    if (lane < SPAN && T.ty + lane < D.tiles_y) {
+        TileState *t = P.tiles + g + lane * D.tiles_x;
+        *(volatile int *)&t->epoch = 0;
+        *(volatile int *)&t->active = 0;
+        __stcg(cnt + lane, 0);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fsum += __shfl_down_sync(FULL_MASK, fsum, o);
+        bad |= __shfl_down_sync(FULL_MASK, bad, o);
+    }
+    __threadfence();
+    if (lane == 0) {
+        if (fsum) atomicAdd(&P.ist[inst].flow, (unsigned long long)fsum);
+        if (bad) {
+            atomicOr(&P.ist[inst].vflags, bad);
+            atomicCAS(&P.ist[inst].status, PMF_OK, flags_status(bad));
+        }
+    }
+}
+
+// Start a posted slot: its instance state is reset and its strips are queued
+// for the set-up pass, into the same ring every running instance uses.  Run
+// by the warp that took the slot from the mailbox.
+template <bool SV>
+__device__ void admit(const Params &P, int slot) {
+    const int lane = threadIdx.x & 31;
+    volatile InstState *S = P.ist + slot;
+    const DevInst D = load_inst<SV>(P, slot);
+    if (lane == 0) {
+        S->phase = PH_SETUP;
+        S->k = 0;
+        S->epoch = 1;
+        S->status = PMF_OK;
+        S->vflags = 0;
+        S->pr_budget = D.n_tiles;
+        S->want_bfs = 0;
+        S->lab_cap = D.hcap;
+        S->pr_mark = 0;
+        S->step_mark = 0;
+        S->epochs = 1;
+        S->lam_prev = 0;
+        S->active = 0;
+        S->dmax = 0;
+        S->flow = 0;
+        S->pr_visits = 0;
+        S->bfs_visits = 0;
+        S->warm_visits = 0;
+        S->outstanding = 1;              // guard while the strips are queued
+        __threadfence();
+    }
+    __syncwarp();
+    enqueue_tiles(P, slot, D, false, true);
+    int last = 0;
+    if (lane == 0) {
+        __threadfence();
+        last = atomicAdd(&P.ist[slot].outstanding, -1) == 1;
+    }
+    if (__shfl_sync(FULL_MASK, last, 0)) transition<SV>(P, slot);
+}
+
+constexpr unsigned long long NO_TICKET = ~0ULL;
+constexpr unsigned long long MB_POLL_NS = 20000;   // mailbox checks: one every 20 us at most
+
+// server mode pop: a worker keeps its ticket across calls; while its slot is
+// empty it looks at the mailbox now and then.  Returns an item, -1 to stop,
+// or -2 - slot for a posted slot the warp must admit.
+__device__ int ring_pop_server(const Params &P, unsigned long long &ticket) {   // one lane
+    Globals *G = P.g;
+    if (ticket == NO_TICKET) ticket = atomicAdd(&G->head, 1ULL);
+    volatile int *slot = (volatile int *)(P.ring + (ticket & P.ring_mask));
+    Mailbox *MB = P.mailbox;
+    unsigned ns = 32;
+    unsigned long long last_tail = ~0ULL, last_prog = ~0ULL, t_since = 0;
+    int last_done = -1;
+    for (unsigned polls = 1;; ++polls) {
+        const int v = *slot;
+        if (v != -1) {
+            *slot = -1;
+            __threadfence();
+            ticket = NO_TICKET;
+            return v;
+        }
+        if ((polls & 3) == 0) {
+            if (ldv(&G->err)) return -1;
+            const unsigned long long now = gtime_ns();
+            if (now - ldv64(&G->t_start) > (unsigned long long)P.max_ns) {
+                atomicOr(&G->err, GE_TIMEOUT);
+                return -1;
+            }
+            // one warp at a time looks at the mailbox (a load over PCIe): many
+            // outstanding loads of host memory hold up the SMs' memory queues
+            // for the warps that are working
+            const unsigned long long due = ldv64(&G->mb_next_ns);
+            if (now >= due && atomicCAS(&G->mb_next_ns, due, now + MB_POLL_NS) == due) {
+                int tail;
+                asm volatile("ld.acquire.sys.global.b32 %0, [%1];" : "=r"(tail) : "l"(&MB->tail) : "memory");
+                const int h = ldv(&G->cmd_head);
+                if (h < tail && atomicCAS(&G->cmd_head, h, h + 1) == h) {
+                    atomicAdd(&G->admitted, 1);
+                    return -2 - *(volatile int *)&MB->ring[h % MB_CAP];
+                }
+                if (*(volatile int *)&MB->stop && h >= tail && ldv(&G->inst_done) >= ldv(&G->admitted))
+                    return -1;
+            }
+            // the stall watchdog counts only while admitted work is unfinished
+            const int ndone = ldv(&G->inst_done);
+            const unsigned long long tl = ldv64(&G->tail), pg = ldv64(&G->progress);
+            if (ndone >= ldv(&G->admitted) || tl != last_tail || ndone != last_done || pg != last_prog) {
+                last_tail = tl;
+                last_done = ndone;
+                last_prog = pg;
+                t_since = now;
+            } else if (now - t_since > (unsigned long long)P.stall_ns) {
+                atomicOr(&G->err, GE_STALL);
+                return -1;
+            }
+        }
+        __nanosleep(ns);
+        if (ns < (unsigned)P.poll_ns) ns <<= 1;
+    }
+}
+
+// --------------------------------------------------------------------------
 // persistent worker
 // --------------------------------------------------------------------------
 constexpr int WORKER_WARPS = 4;
 
-template <int TH, int PO, bool SINK>
+template <int TH, int PO, bool SINK, bool SV>
 // at least 4 resident blocks per SM at tile height 4 (128 registers) and 2 at
 // height 8: with fewer, throughput-bound batches lose more than the spills cost.
 // SINK: the batch holds instances whose sink capacities fall with lambda
-// (their own kernels, so that the others' register allocation is untouched)
+// (their own kernels, so that the others' register allocation is untouched).
+// SV: the server kernel (instances admitted from the mailbox while it runs)
 __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_kernel(const __grid_constant__ Params P) {
     __shared__ WarpSmem<TH> smem[WORKER_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1358,6 +1699,7 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_ker
     unsigned long long tw = 0, tpr = 0, tbfs = 0, tfin = 0, t0 = prof ? gtime_ns() : 0;
     int next = -1;           // an item kept by the last finish, run without queueing
     unsigned chain = 0;
+    unsigned long long ticket = NO_TICKET;   // server mode: a ticket kept across admissions
     for (;;) {
         int g = 0;
         if (next >= 0) {
@@ -1375,8 +1717,16 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_ker
             }
         } else {
             chain = 0;
-            if (lane == 0) g = round_mode ? ring_pop_round(P) : ring_pop_ticket(P);
+            if constexpr (SV) {
+                if (lane == 0) g = ring_pop_server(P, ticket);
+            } else {
+                if (lane == 0) g = round_mode ? ring_pop_round(P) : ring_pop_ticket(P);
+            }
             g = __shfl_sync(FULL_MASK, g, 0);
+            if (SV && g <= -2) {
+                admit<SV>(P, -2 - g);
+                continue;
+            }
         }
         if (prof) { const unsigned long long t1 = gtime_ns(); tw += t1 - t0; t0 = t1; }
         if (g < 0) break;
@@ -1386,7 +1736,7 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_ker
             __threadfence();
         }
         __syncwarp();
-        const DevInst D = load_inst(P, inst);
+        const DevInst D = load_inst<SV>(P, inst);
         // phase, k, epoch, status in one 16-byte load
         int phase, k, epoch, status;
         asm volatile("ld.volatile.global.v4.s32 {%0, %1, %2, %3}, [%4];"
@@ -1396,15 +1746,18 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_ker
         unsigned nb = 0;
         // a relabel item must be a strip's leader tile: anything else means a
         // push/relabel item outlived its phase, which the phase changes rule out
-        const bool strip = phase == PH_BFS || phase == PH_FWD || phase == PH_WARM;
+        const bool strip = phase == PH_BFS || phase == PH_FWD || phase == PH_WARM || phase == PH_COPY ||
+                           phase == PH_SETUP;
         const bool stray = strip && ((g - D.tile_base) / D.tiles_x) % (BFS_ROWS / TH) != 0;
         if (stray && lane == 0) atomicOr(&P.g->err, GE_PHASE);
-        if (status == PMF_OK && phase == PH_PR) pr_visit<TH, PO>(P, S, g, inst, D, k, requeue, nb);
+        if (status == PMF_OK && phase == PH_PR) pr_visit<TH, PO, SV>(P, S, g, inst, D, k, requeue, nb);
         else if (status == PMF_OK && phase == PH_BFS && !stray)
-            bfs_visit<TH, false>(P, S, g, inst, D, epoch, k, requeue, nb);
+            bfs_visit<TH, false, SV>(P, S, g, inst, D, epoch, k, requeue, nb);
         else if (status == PMF_OK && phase == PH_FWD && !stray)
-            bfs_visit<TH, true>(P, S, g, inst, D, epoch, k, requeue, nb);
-        else if (status == PMF_OK && phase == PH_WARM && !stray) warm_visit<TH, SINK>(P, g, inst, D, k);
+            bfs_visit<TH, true, SV>(P, S, g, inst, D, epoch, k, requeue, nb);
+        else if (status == PMF_OK && phase == PH_WARM && !stray) warm_visit<TH, SINK, SV>(P, g, inst, D, k);
+        else if (status == PMF_OK && phase == PH_COPY && !stray) copy_visit<TH, SV>(P, g, inst, D);
+        else if (SV && phase == PH_SETUP && !stray) setup_visit<TH>(P, g, inst, D);
         __threadfence();
         __syncwarp();
         if (prof) {
@@ -1413,7 +1766,7 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_ker
             t0 = t1;
         }
         // in host-polled rounds every new item waits for the next round
-        next = finish(P, g, inst, phase, requeue, nb, D, round_mode == 0);
+        next = finish<SV>(P, g, inst, phase, requeue, nb, D, round_mode == 0);
         if (prof) { const unsigned long long t1 = gtime_ns(); tfin += t1 - t0; t0 = t1; }
     }
     if (prof && lane == 0) {
@@ -1482,7 +1835,7 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
     const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const size_t cap = (size_t)P.ring_mask + 1;
     for (size_t i = t0; i < cap; i += stride)
-        if (i >= (size_t)P.n_leads_total) P.ring[i] = -1;
+        if (i >= (size_t)P.n_leads_queued) P.ring[i] = -1;
 
     const int span = BFS_ROWS / P.tile_h;
     // one thread per tile: its instance is the last one whose first tile is
@@ -1498,17 +1851,20 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
         const int j = (int)(g - (size_t)__ldg(&P.inst[lo].tile_base));
         const int ty = j / tiles_x, tx = j - ty * tiles_x;
         const bool lead = (ty % span) == 0;
+        // a forked instance's strips are queued by its parent's copy pass
+        const bool waits = __ldg(&P.inst[lo].fork_parent) >= 0;
         ((int32_t *)P.tile_inst)[g] = lo;
         TileState t;
-        t.state = lead ? T_QUEUED : T_IDLE;
+        t.state = (lead && !waits) ? T_QUEUED : T_IDLE;
         t.epoch = 0;
         t.pad_ = 0;
         t.active = 0;
         P.tiles[g] = t;
-        // every relabel strip of every instance is queued for the first relabel
+        // every relabel strip of every instance is queued for the first
+        // relabel, except those of forked instances (numbered last)
         if (lead) {
             const size_t strip = (size_t)__ldg(&P.inst[lo].lead_base) + (size_t)(ty / span) * tiles_x + tx;
-            P.ring[strip] = (int)g;
+            if (!waits) P.ring[strip] = (int)g;
             // the strip record's copy of its tiles' active counts starts with them, at 0
             int32_t *cnt = P.strip_cache + strip * STRIP_REC_WORDS + RW_CNT * 32;
             for (int j = 0; j < span; ++j) cnt[j] = 0;
@@ -1516,21 +1872,23 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
     }
     for (size_t i = t0; i < (size_t)P.n_inst; i += stride) {
         const DevInst D = P.inst[i];
+        const bool waits = D.fork_parent >= 0;
         InstState s;
-        s.phase = PH_BFS;
+        s.phase = waits ? PH_WAIT : PH_BFS;
         s.k = 0;
         s.epoch = 1;
         s.vflags = P.inst_flags[i] | P.img_flags[D.image];
         s.status = flags_to_status(s.vflags);
         s.pad3_ = 0;
-        s.pad_b_ = s.pad_c_ = 0;
+        s.lam_prev = 0;
+        s.pad_c_ = 0;
         s.pr_mark = 0;
         s.pr_budget = D.n_tiles;
         s.dmax = 0;
         s.lab_cap = D.hcap;
         s.step_mark = 0;
         s.epochs = 1;
-        s.outstanding = D.n_leads;
+        s.outstanding = waits ? 0 : D.n_leads;
         s.active = 0;
         s.want_bfs = 0;
         s.flow = 0;
@@ -1542,7 +1900,7 @@ __global__ void reset_kernel(const __grid_constant__ Params P) {
     if (t0 == 0) {
         Globals *G = P.g;
         G->head = 0;
-        G->tail = (unsigned long long)P.n_leads_total;
+        G->tail = (unsigned long long)P.n_leads_queued;
         G->inst_done = 0;
         G->err = 0;
         G->round_mode = 0;
@@ -1561,12 +1919,16 @@ __global__ void init_kernel(const __grid_constant__ Params P) {
     const DevInst D = P.inst[inst];
     const size_t PS = (size_t)D.rows * D.pitch;
     int32_t *base = P.planes + D.plane_off;
+    // a forked instance takes its state and terminals from its parent's copy
+    // pass; here only its own schedule is checked against those terminals
+    const bool forked = D.fork_parent >= 0;
+    const int32_t *tb = forked ? P.planes + P.inst[D.fork_parent].plane_off : base;
     const int32_t *L = P.lambdas + (size_t)inst * P.max_lambdas;
     const long long lam0 = L[0], lamN = L[D.n_lambda - 1];
     long long fsum = 0;
     int bad = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < PS; i += (size_t)gridDim.x * blockDim.x) {
-        const int s0 = base[P_SRC0 * PS + i], sl = base[P_SLOPE * PS + i], ct = base[P_CT * PS + i];
+        const int s0 = tb[P_SRC0 * PS + i], sl = tb[P_SLOPE * PS + i], ct = tb[P_CT * PS + i];
         // the source capacities rise with lambda, or the sink capacities fall
         // (Section 2.1's monotone case either way): both stay within
         // [0, PMF_INF] over the whole schedule
@@ -1577,6 +1939,7 @@ __global__ void init_kernel(const __grid_constant__ Params P) {
         if (cs0 < 0 || ctN < 0) bad |= VF_NEG;
         if (csN > PMF_INF) bad |= VF_OVERFLOW;
         const bool ok = cs0 >= 0 && ctN >= 0 && csN <= PMF_INF;
+        if (forked) continue;
         int e = ok ? (int)cs0 : 0;
         int rt = ok ? (int)ct0 : 0;
         const int m = min(e, rt);
@@ -1753,19 +2116,76 @@ cudaError_t launch_worker(const Params &P, int grid, cudaStream_t s) {
     const dim3 b(WORKER_WARPS * 32);
     if (P.any_sink_side) {
         if (P.tile_h == 4) {
-            if (P.chain_push) worker_kernel<4, 1, true><<<grid, b, 0, s>>>(P);
-            else worker_kernel<4, 0, true><<<grid, b, 0, s>>>(P);
+            if (P.chain_push) worker_kernel<4, 1, true, false><<<grid, b, 0, s>>>(P);
+            else worker_kernel<4, 0, true, false><<<grid, b, 0, s>>>(P);
         } else {
-            if (P.chain_push) worker_kernel<8, 1, true><<<grid, b, 0, s>>>(P);
-            else worker_kernel<8, 0, true><<<grid, b, 0, s>>>(P);
+            if (P.chain_push) worker_kernel<8, 1, true, false><<<grid, b, 0, s>>>(P);
+            else worker_kernel<8, 0, true, false><<<grid, b, 0, s>>>(P);
         }
     } else if (P.tile_h == 4) {
-        if (P.chain_push) worker_kernel<4, 1, false><<<grid, b, 0, s>>>(P);
-        else worker_kernel<4, 0, false><<<grid, b, 0, s>>>(P);
+        if (P.chain_push) worker_kernel<4, 1, false, false><<<grid, b, 0, s>>>(P);
+        else worker_kernel<4, 0, false, false><<<grid, b, 0, s>>>(P);
     } else {
-        if (P.chain_push) worker_kernel<8, 1, false><<<grid, b, 0, s>>>(P);
-        else worker_kernel<8, 0, false><<<grid, b, 0, s>>>(P);
+        if (P.chain_push) worker_kernel<8, 1, false, false><<<grid, b, 0, s>>>(P);
+        else worker_kernel<8, 0, false, false><<<grid, b, 0, s>>>(P);
     }
+    return cudaGetLastError();
+}
+
+// server mode: tile height 4, pushes along columns and rows
+cudaError_t launch_server_worker(const Params &P, int grid, cudaStream_t s) {
+    (void)cudaGetLastError();
+    worker_kernel<4, 1, false, true><<<grid, WORKER_WARPS * 32, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t server_occupancy(int *blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<4, 1, false, true>,
+                                                         WORKER_WARPS * 32, 0);
+}
+
+// every tile idle and owned by its slot, the ring empty, every slot finished
+__global__ void server_reset_kernel(const __grid_constant__ Params P, int max_tiles) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    for (size_t i = t0; i <= (size_t)P.ring_mask; i += stride) P.ring[i] = -1;
+    for (size_t g = t0; g < (size_t)P.n_tiles_total; g += stride) {
+        ((int32_t *)P.tile_inst)[g] = (int32_t)(g / (size_t)max_tiles);
+        TileState t;
+        t.state = T_IDLE;
+        t.epoch = 0;
+        t.pad_ = 0;
+        t.active = 0;
+        P.tiles[g] = t;
+    }
+    for (size_t i = t0; i < (size_t)P.n_inst; i += stride) {
+        InstState s;
+        memset(&s, 0, sizeof(s));
+        s.phase = PH_DONE;
+        s.status = PMF_OK;
+        P.ist[i] = s;
+    }
+    if (t0 == 0) {
+        Globals *G = P.g;
+        G->head = 0;
+        G->tail = 0;
+        G->inst_done = 0;
+        G->err = 0;
+        G->round_mode = 0;
+        G->round_end = 0;
+        G->t_start = gtime_ns();
+        G->progress = 0;
+        G->trace_n = 0;
+        G->cmd_head = 0;
+        G->admitted = 0;
+        G->mb_next_ns = 0;
+        for (int j = 0; j < PMF_PROFILE_COUNTERS; ++j) G->prof[j] = 0;
+    }
+}
+
+cudaError_t launch_server_reset(const Params &P, int max_tiles, cudaStream_t s) {
+    (void)cudaGetLastError();
+    server_reset_kernel<<<1024, 256, 0, s>>>(P, max_tiles);
     return cudaGetLastError();
 }
 
@@ -1779,8 +2199,10 @@ int worker_warps_per_block() { return WORKER_WARPS; }
 
 cudaError_t worker_occupancy(int tile_h, int *blocks_per_sm) {
     if (tile_h == 4)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<4, 0, false>, WORKER_WARPS * 32, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<8, 0, false>, WORKER_WARPS * 32, 0);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<4, 0, false, false>,
+                                                             WORKER_WARPS * 32, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<8, 0, false, false>,
+                                                         WORKER_WARPS * 32, 0);
 }
 
 }  // namespace pmf

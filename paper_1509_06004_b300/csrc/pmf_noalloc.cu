@@ -153,6 +153,7 @@ extern "C" PMF_API pmf_status pmf_solve_noalloc(int32_t H, int32_t W, const int3
     d.hcap = H * W + 1;
     d.lead_base = 0;
     d.n_leads = tiles_x * ((tiles_y + BFS_ROWS / kTileH - 1) / (BFS_ROWS / kTileH));
+    d.fork_parent = d.fork_child = d.fork_k = -1;
 
     Params P;
     std::memset(&P, 0, sizeof(P));
@@ -175,6 +176,7 @@ extern "C" PMF_API pmf_status pmf_solve_noalloc(int32_t H, int32_t W, const int3
     P.n_inst = 1;
     P.n_tiles_total = n_tiles;
     P.n_leads_total = d.n_leads;
+    P.n_leads_queued = d.n_leads;
     P.max_lambdas = n_lambda;
     P.sweeps = kSweeps;
     P.chain_push = kPushOrder;

@@ -158,6 +158,9 @@ class Instance:
     # for a piece of a split schedule: (index of the instance it was cut from,
     # int array of the positions of its lambdas in that instance's schedule)
     origin: tuple | None = None
+    # for a forked piece: (index of the parent instance in the same workload,
+    # the parent's step after which this piece starts from its state)
+    fork: tuple | None = None
 
 
 @dataclass
@@ -211,6 +214,29 @@ class Workload:
                 raise ValueError(f"pieces {lengths} do not cover a schedule of {len(inst.lambdas)}")
             for part in np.split(np.arange(len(inst.lambdas)), np.cumsum(lengths)[:-1]):
                 out.instances.append(self._piece(i, inst, part))
+        return out
+
+    def split_forked(self, segments: int, lead: int) -> "Workload":
+        """Every instance's schedule cut into ``segments`` consecutive pieces
+        (as split_segments), each piece after the first FORKED from the one
+        before: it starts from that piece's state once the piece has
+        certified its step (length - 1 - lead), instead of cold.  lead = 0
+        forks after the previous piece's last step (a chain, as one piece);
+        a larger lead starts the next piece that many steps earlier, so the
+        two run side by side, the new piece warm-started from a lambda
+        ``lead + 1`` steps below its first."""
+        if lead < 0:
+            raise ValueError("lead >= 0")
+        out = self.split_segments(segments)
+        out.name = self.name + f"/fork{segments}x{lead}"
+        first = 0
+        for inst in self.instances:
+            n = segments
+            for j in range(1, n):
+                prev = out.instances[first + j - 1]
+                step = max(0, len(prev.lambdas) - 1 - lead)
+                out.instances[first + j].fork = (first + j - 1, step)
+            first += n
         return out
 
     def split_interleaved(self, stride: int) -> "Workload":

@@ -40,7 +40,10 @@ EXPORTS = ["pmf_workspace_size", "pmf_create_batch", "pmf_set_tuning", "pmf_get_
            "pmf_get_stats", "pmf_get_trace", "pmf_get_profile", "pmf_get_mask_layout",
            "pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error",
            "pmf_solve_noalloc", "pmf_get_flow_arcs", "pmf_set_cut_rule",
-           "pmf_set_slope_side", "pmf_testing_fail_noalloc_call"]
+           "pmf_set_slope_side", "pmf_testing_fail_noalloc_call", "pmf_cut_lines",
+           "pmf_restrict_between", "pmf_set_fork", "pmf_server_workspace_size", "pmf_server_create",
+           "pmf_server_set_tuning", "pmf_server_start", "pmf_server_load", "pmf_server_post", "pmf_server_poll",
+           "pmf_server_read", "pmf_server_stop", "pmf_server_destroy"]
 
 
 class PmfError(RuntimeError):
@@ -70,6 +73,11 @@ class Tuning(ctypes.Structure):
                 ("poll_ns", ctypes.c_int32), ("label_slack", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("push_order", ctypes.c_int32),
                 ("relabel_extra", ctypes.c_int32)]
+
+
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("max_h", ctypes.c_int32), ("max_w", ctypes.c_int32),
+                ("max_lambdas", ctypes.c_int32), ("device", ctypes.c_int32)]
 
 
 class TraceEvent(ctypes.Structure):
@@ -125,6 +133,7 @@ def lib(path: str | None = None):
             L.pmf_get_flow_arcs.argtypes = [vp, i32, vp, vp, vp, vp]
             L.pmf_set_cut_rule.argtypes = [vp, i32, i32]
             L.pmf_set_slope_side.argtypes = [vp, i32, i32]
+            L.pmf_set_fork.argtypes = [vp, i32, i32, i32]
             L.pmf_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
             L.pmf_get_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
             L.pmf_get_trace.argtypes = [vp, ctypes.POINTER(TraceEvent), i32, i32p]
@@ -137,13 +146,28 @@ def lib(path: str | None = None):
             L.pmf_version.restype = ctypes.c_char_p
             L.pmf_solve_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32p, i32, vp,
                                             ctypes.POINTER(ctypes.c_int64), vp]
+            L.pmf_cut_lines.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp]
+            L.pmf_restrict_between.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int64,
+                                               ctypes.c_int64, vp, vp, vp, vp, vp, vp]
+            sdp = ctypes.POINTER(ServerDesc)
+            L.pmf_server_workspace_size.argtypes = [sdp, ctypes.POINTER(ctypes.c_size_t)]
+            L.pmf_server_create.argtypes = [sdp, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+            L.pmf_server_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+            L.pmf_server_start.argtypes = [vp, ctypes.c_double]
+            L.pmf_server_load.argtypes = [vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, i32]
+            L.pmf_server_post.argtypes = [vp, vp, i32]
+            L.pmf_server_poll.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
+            L.pmf_server_read.argtypes = [vp, i32, vp, vp]
+            L.pmf_server_stop.argtypes = [vp]
+            L.pmf_server_destroy.argtypes = [vp]
+            L.pmf_server_destroy.restype = None
             L.pmf_testing_fail_noalloc_call.argtypes = [i32]
             L.pmf_testing_fail_noalloc_call.restype = None
             L.pmf_last_error.argtypes = []
             L.pmf_last_error.restype = ctypes.c_char_p
             for name in EXPORTS:
                 if name not in ("pmf_destroy_batch", "pmf_status_string", "pmf_version", "pmf_last_error",
-                                "pmf_testing_fail_noalloc_call"):
+                                "pmf_testing_fail_noalloc_call", "pmf_server_destroy"):
                     getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -347,6 +371,11 @@ class Batch:
         (see pmf_set_cut_rule); cuts then come back for the original problem."""
         _check(lib().pmf_set_cut_rule(self._h, int(inst), int(rule)), "pmf_set_cut_rule")
 
+    def set_fork(self, child: int, parent: int, parent_step: int) -> None:
+        """child starts from parent's state once parent has certified its
+        step parent_step (see pmf_set_fork); parent = -1 removes the fork."""
+        _check(lib().pmf_set_fork(self._h, int(child), int(parent), int(parent_step)), "pmf_set_fork")
+
     def set_slope_side(self, inst: int, side: int) -> None:
         """0: source capacities src0 + slope*lambda rise with lambda (default);
         1: sink capacities sink - slope*lambda fall (see pmf_set_slope_side)."""
@@ -423,6 +452,91 @@ class Batch:
             pass
 
 
+def server_workspace_size(n_slots: int, max_h: int, max_w: int, max_lambdas: int, device: int = 0) -> int:
+    """Device bytes of a server (no GPU needed)."""
+    d = ServerDesc(n_slots, max_h, max_w, max_lambdas, device)
+    n = ctypes.c_size_t(0)
+    _check(lib().pmf_server_workspace_size(ctypes.byref(d), ctypes.byref(n)), "pmf_server_workspace_size")
+    return int(n.value)
+
+
+class Server:
+    """A running server kernel with instance slots (pmf_server_*): load
+    instances into free slots and post them while it runs; poll and read
+    finished ones."""
+
+    def __init__(self, n_slots: int, max_h: int, max_w: int, max_lambdas: int, device: int = 0,
+                 workspace=None, **tuning):
+        import torch
+        self.n_slots, self.max_h, self.max_w, self.max_lambdas = int(n_slots), int(max_h), int(max_w), int(max_lambdas)
+        self.device = int(device)
+        d = ServerDesc(self.n_slots, self.max_h, self.max_w, self.max_lambdas, self.device)
+        self.workspace_bytes = server_workspace_size(n_slots, max_h, max_w, max_lambdas, device)
+        if workspace is None:
+            workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=f"cuda:{self.device}")
+        self.workspace = workspace
+        h = ctypes.c_void_p(0)
+        _check(lib().pmf_server_create(ctypes.byref(d), ctypes.c_void_p(workspace.data_ptr()), self.workspace_bytes,
+                                       ctypes.byref(h)), "pmf_server_create")
+        self._h = h
+        self.shape = {}
+        self._keep = {}
+        if tuning:
+            t = Tuning()
+            for k, v in tuning.items():
+                setattr(t, k, int(v))
+            _check(lib().pmf_server_set_tuning(self._h, ctypes.byref(t)), "pmf_server_set_tuning")
+
+    def start(self, max_seconds: float = 600.0):
+        _check(lib().pmf_server_start(self._h, float(max_seconds)), "pmf_server_start")
+
+    def load(self, slot: int, image_slot: int, w_h, w_v, src0, slope, sink, lambdas):
+        c = lambda a: np.ascontiguousarray(a, np.int32) if a is not None else None
+        src0, slope, sink = c(src0), c(slope), c(sink)
+        H, W = src0.shape
+        w_h, w_v = c(w_h), c(w_v)
+        lam = np.ascontiguousarray(lambdas, np.int32)
+        p = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
+        st = lib().pmf_server_load(self._h, int(slot), int(image_slot), H, W, p(w_h), p(w_v), p(src0), p(slope),
+                                   p(sink), lam.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(lam))
+        _check(st, "pmf_server_load")
+        self.shape[int(slot)] = (H, W, len(lam))
+
+    def post(self, slots):
+        a = np.ascontiguousarray(slots, np.int32)
+        _check(lib().pmf_server_post(self._h, ctypes.c_void_p(a.ctypes.data), len(a)), "pmf_server_post")
+
+    def poll(self) -> np.ndarray:
+        done = np.zeros(self.n_slots, np.uint8)
+        _check(lib().pmf_server_poll(self._h, ctypes.c_void_p(done.ctypes.data), None), "pmf_server_poll")
+        return done.astype(bool)
+
+    def read(self, slot: int, check: bool = True):
+        """(status, flows [m], masks [m, H, W]) of a finished slot; frees it."""
+        H, W, m = self.shape[int(slot)]
+        masks = np.empty((m, H, W), np.uint8)
+        flows = np.empty(m, np.int64)
+        st = lib().pmf_server_read(self._h, int(slot), ctypes.c_void_p(masks.ctypes.data),
+                                   ctypes.c_void_p(flows.ctypes.data))
+        if check:
+            _check(st, "pmf_server_read")
+        return st, flows, masks
+
+    def stop(self) -> int:
+        return lib().pmf_server_stop(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().pmf_server_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def batch_from_workload(wl, device: int = 0, stream=None, device_inputs: bool = False,
                         workspace=None, **tuning) -> Batch:
     """A Batch holding every image and instance of an inputs.Workload, with all
@@ -438,9 +552,14 @@ def batch_from_workload(wl, device: int = 0, stream=None, device_inputs: bool = 
         if device_inputs else (lambda a: a)
     for i, im in enumerate(wl.images):
         b.set_capacities(i, conv(im.w_h), conv(im.w_v))
-    # pieces of one problem (the same terminal arrays) are uploaded once
+    # pieces of one problem (the same terminal arrays) are uploaded once; a
+    # forked piece takes its parent's terminals with its state
     first = {}
     for i, inst in enumerate(wl.instances):
+        fork = getattr(inst, "fork", None)
+        if fork is not None:
+            b.set_fork(i, fork[0], fork[1])
+            continue
         key = (inst.image, id(inst.src0), id(inst.slope), id(inst.sink))
         if key in first:
             b.copy_terminals(i, first[key])

@@ -2,19 +2,28 @@
 
 Each request is one image with its seeds and its lambda schedule (the paper's
 per-image figure-ground stage, Section 4).  Requests arrive over time; the
-server keeps up to ``slots`` of them on the GPU at once, each on its own
-stream with its own share of the SMs, so their work overlaps on the device.  A
-request is admitted (first come, first served) as soon as a slot is free AND
-its device workspace fits in what is left of the memory budget; its residual
-state stays resident on the device across its whole lambda schedule; when it
-finishes its masks and flows are read back, its slot and memory are released
-and the next waiting request is admitted at once.  This is the GPU analogue of
+server keeps up to ``slots`` of them on the GPU at once, and their work
+overlaps on the device.  A request is admitted (first come, first served) as
+soon as a slot is free AND its device memory fits in what is left of the
+budget; its residual state stays resident on the device across its whole
+lambda schedule; when it finishes its masks and flows are read back, its slot
+and memory are released and the next waiting request is admitted at once.  This is the GPU analogue of
 the paper's dynamic scheduler, which hands the next supergraph to whichever
 server frees up first (Section 3.3.1), and of its overlap of one call's
 transfer with another's computation (Section 3.3.2).
 
-The scheduler is plain host logic over a backend (``GpuBackend`` runs the
-CUDA solver through the C ABI; tests use a fake backend on the CPU).
+The scheduler is plain host logic over a backend; tests use a fake backend on
+the CPU.  Two GPU backends:
+
+* ``LiveBackend`` (the default): ONE server kernel (pmf_server_*) keeps running;
+  a request's seeds are loaded into free instance slots while it runs and
+  posted to it, an idle worker of the kernel admits them into the device work
+  queue that every running instance shares, and finished slots are read back
+  while the others run.  A lone request gets the whole GPU; several mix in
+  one queue, with no static share of the SMs.
+* ``GpuBackend``: each request as its own batch and persistent launch on a
+  stream of its own, with a fixed share of the SMs per slot.
+
 Latency of a request = completion (results on the host) - arrival.
 """
 from __future__ import annotations
@@ -238,8 +247,96 @@ class GpuBackend:
         return (flows, masks) if collect else (None, None)
 
 
-def serve(requests, slots: int = 4, budget_bytes: int = 64 << 30, device: int = 0, realtime: bool = True,
-          collect: bool = False, segments: int | None = None, tuning: dict | None = None) -> ServeStats:
-    """Serve a request stream with continuous batching; returns ServeStats."""
+class LiveBackend:
+    """Requests as instances of one running server kernel: each seed of a
+    request takes an instance slot (the first one holds the request's image,
+    the others use it), the slots are loaded while the kernel runs and posted
+    to it together; the request is done when all its slots are, and its slots
+    are freed when it has been read.  Admission is by free slots: the server
+    has as many as the memory budget holds (at most ``max_slots``)."""
+
+    def __init__(self, budget_bytes: int, device: int = 0, max_h: int = 600, max_w: int = 800,
+                 max_lambdas: int = 30, max_slots: int = 512, tuning: dict | None = None,
+                 max_seconds: float = 900.0):
+        from . import pmf
+        self.pmf = pmf
+        per = pmf.server_workspace_size(2, max_h, max_w, max_lambdas, device) - \
+            pmf.server_workspace_size(1, max_h, max_w, max_lambdas, device)
+        self.slot_bytes = per
+        n = int(max(1, min(max_slots, budget_bytes // max(per, 1))))
+        tuning = dict(tuning or {})
+        tuning.setdefault("label_slack", 8)
+        self.server = pmf.Server(n, max_h, max_w, max_lambdas, device, **tuning)
+        self.server.start(max_seconds)
+        self.free = list(range(n))[::-1]
+        self.n_slots = n
+        self._done = None
+
+    def bytes(self, req) -> int:
+        return len(req.workload.instances) * self.slot_bytes
+
+    def reserve(self, req):
+        k = len(req.workload.instances)
+        if k > self.n_slots:
+            raise ValueError("a request with more seeds than the server has slots")
+        if len(self.free) < k:
+            return None
+        return [self.free.pop() for _ in range(k)]
+
+    def release(self, tok) -> None:
+        self.free.extend(tok)
+
+    def in_use(self) -> int:
+        return (self.n_slots - len(self.free)) * self.slot_bytes
+
+    def start(self, req, slot, tok):
+        wl = req.workload
+        im = wl.images[0]
+        for j, inst in enumerate(wl.instances):
+            first = j == 0
+            self.server.load(tok[j], tok[0], im.w_h if first else None, im.w_v if first else None,
+                             inst.src0, inst.slope, inst.sink, inst.lambdas)
+        self.server.post(tok)
+        return (tok, req)
+
+    def done(self, h) -> bool:
+        d = self.server.poll()
+        return bool(all(d[s] for s in h[0]))
+
+    def finish(self, h, collect: bool):
+        tok, req = h
+        flows, masks, bad = [], [], []
+        for s in tok:
+            st, f, m = self.server.read(s, check=False)
+            bad.append(st)
+            flows.append(f)
+            masks.append(m)
+        if any(x != self.pmf.PMF_OK for x in bad):
+            raise RuntimeError(f"request failed: {[self.pmf.status_string(x) for x in bad]}")
+        return (flows, masks) if collect else (None, None)
+
+    def close(self) -> int:
+        st = self.server.stop()
+        self.server.close()
+        return st
+
+
+def serve(requests, slots: int = 8, budget_bytes: int = 64 << 30, device: int = 0, realtime: bool = True,
+          collect: bool = False, segments: int | None = None, tuning: dict | None = None,
+          live: bool = True, max_slots: int = 512) -> ServeStats:
+    """Serve a request stream with continuous batching; returns ServeStats.
+    live=True: one running server kernel, at most ``slots`` requests admitted
+    at once (and as many seeds as the budget's instance slots hold);
+    live=False: one batch and launch per request, ``slots`` of them at once."""
+    if live:
+        max_h = max(r.workload.images[0].H for r in requests)
+        max_w = max(r.workload.images[0].W for r in requests)
+        max_l = max(len(i.lambdas) for r in requests for i in r.workload.instances)
+        backend = LiveBackend(budget_bytes, device, max_h, max_w, max_l, max_slots, tuning)
+        try:
+            return Scheduler(backend, slots, budget_bytes).run(requests, realtime=realtime, collect=collect)
+        finally:
+            if backend.close() != 0:
+                raise RuntimeError("the server kernel stopped on a watchdog")
     backend = GpuBackend(slots, budget_bytes, device, segments, tuning)
     return Scheduler(backend, slots, budget_bytes).run(requests, realtime=realtime, collect=collect)

@@ -106,7 +106,11 @@ def test_device_arena_first_fit_and_merge():
 
 
 @pytest.mark.gpu
-def test_continuous_batching_equals_alone():
+@pytest.mark.parametrize("live", [True, False])
+def test_continuous_batching_equals_alone(live):
+    """Requests served while others run (live: admitted into one running
+    server kernel; else: one launch per request on its own stream) give
+    exactly the results of solving each request alone."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -117,7 +121,7 @@ def test_continuous_batching_equals_alone():
         r.workload.instances = r.workload.instances[:4]
         for inst in r.workload.instances:
             inst.lambdas = inst.lambdas[:6]
-    st = serving.serve(reqs, slots=3, budget_bytes=1 << 30, realtime=True, collect=True, segments=2)
+    st = serving.serve(reqs, slots=3, budget_bytes=1 << 30, realtime=True, collect=True, segments=2, live=live)
     assert st.max_concurrent >= 2
     for c, r in zip(st.completed, reqs):
         status, alone = pmf.solve_workload(r.workload)
@@ -144,8 +148,8 @@ def test_serving_large_mix_repeated():
         r.workload.instances = r.workload.instances[:8]
         for inst in r.workload.instances:
             inst.lambdas = inst.lambdas[:10]
-    runs = [serving.serve(reqs, slots=4, budget_bytes=8 << 30, realtime=False, collect=True, segments=5)
-            for _ in range(3)]
+    runs = [serving.serve(reqs, slots=4, budget_bytes=8 << 30, realtime=False, collect=True, segments=5, live=live)
+            for live in (True, True, False)]
     assert runs[0].max_concurrent >= 2
     for i, r in enumerate(reqs):
         status, alone = pmf.solve_workload(r.workload)
@@ -167,3 +171,89 @@ def test_serving_large_mix_repeated():
         c = runs[-1].completed[i]
         assert int(c.flows[j][k]) == int(f[0])
         assert np.array_equal(c.masks[j][k].reshape(-1), np.asarray(m[0]).reshape(-1))
+
+
+@pytest.mark.gpu
+def test_server_slots_bad_inputs_and_reuse():
+    """The server kernel keeps running across requests: a slot loaded with a
+    negative capacity reports PMF_ERR_INVALID_ARG while its neighbours are
+    solved; the freed slots then take new instances (one sharing another
+    slot's image), whose results equal the oracle's; a slot can be read only
+    once it has finished; the server stops cleanly."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1509_06004_b300 import build, pmf
+    build.build()
+    reqs = inputs.serving_stream(rate_per_s=1000.0, n_requests=3, seed=8, max_side=240)
+    srv = pmf.Server(6, 180, 240, 12)
+    srv.start(120.0)
+    try:
+        wl = reqs[0].workload
+        im = wl.images[0]
+        bad = wl.instances[1].sink.copy()
+        bad[3, 3] = -1
+        srv.load(0, 0, im.w_h, im.w_v, wl.instances[0].src0, wl.instances[0].slope, wl.instances[0].sink,
+                 wl.instances[0].lambdas[:5])
+        srv.load(1, 0, None, None, wl.instances[1].src0, wl.instances[1].slope, bad, wl.instances[1].lambdas[:5])
+        assert srv.read(0, check=False)[0] == pmf.PMF_ERR_NOT_READY     # loaded, not posted
+        srv.post([0, 1])
+        import time
+        t0 = time.time()
+        while not (srv.poll()[0] and srv.poll()[1]) and time.time() - t0 < 60:
+            time.sleep(0.001)
+        st0, f0, m0 = srv.read(0)
+        assert st0 == pmf.PMF_OK
+        assert srv.read(1, check=False)[0] == pmf.PMF_ERR_INVALID_ARG
+        inst = wl.instances[0]
+        of, om = oracle.grid_solve(im.H, im.W, im.w_h, im.w_v, inst.src0, inst.slope, inst.sink, inst.lambdas[:5])
+        assert np.array_equal(f0, of) and np.array_equal(m0, om)
+        # reuse: another request's image in slot 1, shared by slot 0
+        wl2 = reqs[1].workload
+        im2 = wl2.images[0]
+        for s, j in ((1, 0), (0, 1)):
+            i2 = wl2.instances[j]
+            srv.load(s, 1, im2.w_h if s == 1 else None, im2.w_v if s == 1 else None, i2.src0, i2.slope, i2.sink,
+                     i2.lambdas[:7])
+        srv.post([1, 0])
+        t0 = time.time()
+        while not (srv.poll()[0] and srv.poll()[1]) and time.time() - t0 < 60:
+            time.sleep(0.001)
+        for s, j in ((1, 0), (0, 1)):
+            st, f, m = srv.read(s)
+            i2 = wl2.instances[j]
+            of, om = oracle.grid_solve(im2.H, im2.W, im2.w_h, im2.w_v, i2.src0, i2.slope, i2.sink, i2.lambdas[:7])
+            assert np.array_equal(f, of) and np.array_equal(m, om)
+    finally:
+        assert srv.stop() == pmf.PMF_OK
+        srv.close()
+
+
+@pytest.mark.gpu
+def test_lone_request_gets_the_whole_gpu():
+    """A lone request on the live server takes about as long as solving it
+    alone in one batch launch (no static share of the SMs), within a margin
+    for the admission path."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import time
+    from paper_1509_06004_b300 import build, pmf
+    build.build()
+    req = inputs.serving_stream(rate_per_s=10.0, n_requests=1, seed=11, max_side=640)[0]
+    req.arrival_s = 0.0
+    wl = req.workload
+    b = pmf.batch_from_workload(wl, tile_h=4, push_order=1, label_slack=8)
+    lam = np.stack([i.lambdas for i in wl.instances])
+    ts = []
+    for _ in range(4):
+        t0 = time.perf_counter()
+        b.solve(lam)
+        b.sync()
+        ts.append(time.perf_counter() - t0)
+    b.close()
+    alone = float(np.median(ts[1:]))
+    st = [serving.serve([req], slots=1, budget_bytes=4 << 30, realtime=False) for _ in range(3)]
+    live = float(np.median([s.completed[0].latency_s for s in st]))
+    assert live < 1.5 * alone + 0.02, (live, alone)
