@@ -641,7 +641,7 @@ def main(argv=None):
     ap.add_argument("--serving-rate", type=float, default=50.0)
     ap.add_argument("--serving-warmup", type=int, default=0, help="leading requests left out of the latencies")
     ap.add_argument("--serving-max-side", type=int, default=800)
-    ap.add_argument("--serving-slots", type=int, default=8, help="requests admitted at once")
+    ap.add_argument("--serving-slots", type=int, default=16, help="requests admitted at once")
     ap.add_argument("--no-serving-batches", action="store_true",
                     help="skip the leg with one launch per request")
     ap.add_argument("--serving-budget", type=int, default=64 << 30)

@@ -321,7 +321,7 @@ class LiveBackend:
         return st
 
 
-def serve(requests, slots: int = 8, budget_bytes: int = 64 << 30, device: int = 0, realtime: bool = True,
+def serve(requests, slots: int = 16, budget_bytes: int = 64 << 30, device: int = 0, realtime: bool = True,
           collect: bool = False, segments: int | None = None, tuning: dict | None = None,
           live: bool = True, max_slots: int = 512) -> ServeStats:
     """Serve a request stream with continuous batching; returns ServeStats.
