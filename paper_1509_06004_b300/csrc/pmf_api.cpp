@@ -904,7 +904,7 @@ pmf_status pmf_get_flow_arcs(pmf_batch *b, int32_t inst, int32_t *f_h, int32_t *
     const int lambda = b->lam_h[(size_t)inst * b->desc.max_lambdas + b->n_lam[inst] - 1];
     int32_t *status_d = (int32_t *)(b->ws + b->L.scratch);
     cudaStream_t s = b->cap_stream;
-    cudaError_t e = launch_return_excess(b->P, d, lambda, 1 << 17, f_h, f_v, f_s, f_t, status_d, s);
+    cudaError_t e = launch_return_excess(b->P, d, lambda, 1 << 17, f_h, f_v, f_s, f_t, status_d, status_d + 4, s);
     int32_t status = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&status, status_d, sizeof(status), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

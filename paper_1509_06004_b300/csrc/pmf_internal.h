@@ -187,9 +187,10 @@ cudaError_t launch_server_reset(const Params &P, int max_tiles, cudaStream_t s);
 cudaError_t launch_server_worker(const Params &P, int grid, cudaStream_t s);
 cudaError_t server_occupancy(int *blocks_per_sm);
 cudaError_t launch_begin_round(const Params &P, cudaStream_t s);
+// flags: 3 int32 of device scratch for the sweeps' termination test
 cudaError_t launch_return_excess(const Params &P, const DevInst &d, int lambda, int max_sweeps,
                                  int32_t *f_h, int32_t *f_v, int32_t *f_s, int32_t *f_t, int32_t *status,
-                                 cudaStream_t s);
+                                 int32_t *flags, cudaStream_t s);
 int worker_warps_per_block();
 // records "where: <CUDA error text>" for pmf_last_error (this thread) and
 // returns PMF_ERR_CUDA; PMF_OK for cudaSuccess

@@ -38,8 +38,12 @@
 // value and the pixels the BFS cannot reach form the maximal source set.
 #include <cstdint>
 
+#include <cooperative_groups.h>
+
 #include "pmf.h"
 #include "pmf_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace pmf {
 
@@ -2024,23 +2028,28 @@ cudaError_t launch_init(const Params &P, int max_pixels, cudaStream_t s) {
 // returning that excess to s turns it into a feasible maximum flow of the
 // same value (Section 2's flow, arc by arc)
 // --------------------------------------------------------------------------
-constexpr int RETURN_THREADS = 1024;
+constexpr int RETURN_THREADS = 512;
 
-// One block.  Start: the preflow with every source arc carrying cs(p) and
-// every sink arc ct(p) - rt(p); a pixel's excess is its inflow minus its
-// outflow.  Sweep: a pixel with excess first sends it back along its own
-// source arc, then back along the pair arcs that carry flow into it (each push
-// lowers a positive flow towards zero).  Only a pair's receiving end ever
-// changes its flow, and no flow changes sign, so the two ends never act on one
-// pair at once.  Every push lowers the sum of |flows| by its amount, so the
-// loop ends; it stops when a whole sweep saw no excess.  The sink arcs never
-// change: the value stays the flow into t.
+// One cooperative grid over the whole GPU.  Start: the preflow with every
+// source arc carrying cs(p) and every sink arc ct(p) - rt(p); a pixel's excess
+// is its inflow minus its outflow.  Sweep: a pixel with excess first sends it
+// back along its own source arc, then back along the pair arcs that carry flow
+// into it (each push lowers a positive flow towards zero).  Only a pair's
+// receiving end ever changes its flow, and no flow changes sign, so the two
+// ends never act on one pair at once; excess moves by atomic adds.  Every
+// push lowers the sum of |flows| by its amount, so the sweeps end; the grid
+// stops after a sweep in which no pixel held excess.  The sink arcs never
+// change: the value stays the flow into t.  Whether a sweep saw excess goes
+// to one of three flags (sweep s uses flag s % 3 and clears flag (s + 1) % 3,
+// whose last readers finished two grid barriers earlier).
 __global__ void __launch_bounds__(RETURN_THREADS) return_excess_kernel(
     const int32_t *E, const int32_t *RT, const int32_t *FR, const int32_t *FD, const int32_t *SRC0,
     const int32_t *SLOPE, const int32_t *CT, int lambda, int slope_side, int H, int W, int pitch, int max_sweeps,
-    int32_t *f_h, int32_t *f_v, int32_t *f_s, int32_t *f_t, int32_t *status) {
+    int32_t *f_h, int32_t *f_v, int32_t *f_s, int32_t *f_t, int32_t *status, int32_t *flags) {
+    cg::grid_group grid = cg::this_grid();
     const int n = H * W;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (int p = tid; p < n; p += nth) {
         const int y = p / W, x = p - y * W;
         const size_t i = (size_t)y * pitch + x;
         f_h[p] = x < W - 1 ? FR[i] : 0;
@@ -2048,13 +2057,15 @@ __global__ void __launch_bounds__(RETURN_THREADS) return_excess_kernel(
         f_s[p] = slope_side ? SRC0[i] : SRC0[i] + SLOPE[i] * lambda;
         f_t[p] = E[i];                      // the excess, until the last step
     }
-    __syncthreads();
+    if (tid == 0) flags[0] = flags[1] = flags[2] = 0;
+    grid.sync();
     volatile int32_t *vh = f_h, *vv = f_v, *vs = f_s, *ve = f_t;
     int sweeps = 0;
     bool more = true;
     while (more && sweeps < max_sweeps) {
+        if (tid == 0) flags[(sweeps + 1) % 3] = 0;
         bool any = false;
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        for (int p = tid; p < n; p += nth) {
             const int ex = ve[p];
             if (ex <= 0) continue;
             any = true;
@@ -2085,29 +2096,46 @@ __global__ void __launch_bounds__(RETURN_THREADS) return_excess_kernel(
             }
             if (ex - rem) atomicSub(&f_t[p], ex - rem);
         }
+        if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&flags[sweeps % 3], 1);
+        __threadfence();
+        grid.sync();
+        more = *(volatile int32_t *)&flags[sweeps % 3] != 0;
         ++sweeps;
-        more = __syncthreads_or(any) != 0;
     }
-    __syncthreads();
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    grid.sync();
+    for (int p = tid; p < n; p += nth) {
         const int y = p / W, x = p - y * W;
         const size_t i = (size_t)y * pitch + x;
         f_t[p] = (slope_side ? CT[i] - SLOPE[i] * lambda : CT[i]) - RT[i];
     }
-    if (threadIdx.x == 0) *status = more ? 1 : 0;
+    if (tid == 0) *status = more ? 1 : 0;
 }
 
 cudaError_t launch_return_excess(const Params &P, const DevInst &d, int lambda, int max_sweeps,
                                  int32_t *f_h, int32_t *f_v, int32_t *f_s, int32_t *f_t, int32_t *status,
-                                 cudaStream_t s) {
+                                 int32_t *flags, cudaStream_t s) {
     const size_t PS = (size_t)d.rows * d.pitch;
     const int32_t *base = P.planes + d.plane_off;
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, return_excess_kernel, RETURN_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    // every block resident at once (a cooperative launch), no more than the pixels need
+    const long long need = ((long long)d.H * d.W + RETURN_THREADS - 1) / RETURN_THREADS;
+    int grid = per_sm * n_sm;
+    if (need < grid) grid = (int)(need < 1 ? 1 : need);
+    const int32_t *E = base + P_E * PS, *RT = base + P_RT * PS, *FR = base + P_FR * PS, *FD = base + P_FD * PS;
+    const int32_t *S0 = base + P_SRC0 * PS, *SL = base + P_SLOPE * PS, *CT = base + P_CT * PS;
+    int lam = lambda, side = d.slope_side, H = d.H, W = d.W, pitch = d.pitch, ms = max_sweeps;
+    void *args[] = {(void *)&E,  (void *)&RT,  (void *)&FR,   (void *)&FD,    (void *)&S0,  (void *)&SL,
+                    (void *)&CT, (void *)&lam, (void *)&side, (void *)&H,     (void *)&W,   (void *)&pitch,
+                    (void *)&ms, (void *)&f_h, (void *)&f_v,  (void *)&f_s,   (void *)&f_t, (void *)&status,
+                    (void *)&flags};
     (void)cudaGetLastError();
-    return_excess_kernel<<<1, RETURN_THREADS, 0, s>>>(base + P_E * PS, base + P_RT * PS, base + P_FR * PS,
-                                                      base + P_FD * PS, base + P_SRC0 * PS, base + P_SLOPE * PS,
-                                                      base + P_CT * PS, lambda, d.slope_side, d.H, d.W, d.pitch, max_sweeps,
-                                                      f_h, f_v, f_s, f_t, status);
-    return cudaGetLastError();
+    return cudaLaunchCooperativeKernel((const void *)return_excess_kernel, dim3(grid), dim3(RETURN_THREADS), args, 0,
+                                       s);
 }
 
 cudaError_t launch_worker(const Params &P, int grid, cudaStream_t s) {

@@ -5,6 +5,10 @@
  *   abi_client solve IN OUT      solve one instance read from IN through a
  *                                batch (pmf_create_batch ... pmf_get_cuts)
  *   abi_client noalloc IN OUT    the same instance through pmf_solve_noalloc
+ *   abi_client server IN OUT     the same instance through a running server
+ *                                kernel (pmf_server_create ... pmf_server_read),
+ *                                loaded twice: into its own slot and into a
+ *                                second slot that uses the first one's image
  *
  * IN (little-endian int32): H, W, n_lambda, lambdas[n_lambda], then H*W each
  * of w_h, w_v, src0, slope, sink.  OUT: n_lambda int64 flows, then
@@ -153,10 +157,52 @@ static int solve_noalloc(const char *in_path, const char *out_path) {
     return rc;
 }
 
+static int solve_server(const char *in_path, const char *out_path) {
+    problem p;
+    int rc = read_problem(in_path, &p);
+    if (rc) return rc;
+    const size_t n = (size_t)p.H * p.W;
+    pmf_server_desc d = {3, p.H, p.W, p.m, 0};
+    size_t bytes = 0;
+    CHECK(pmf_server_workspace_size(&d, &bytes));
+    void *ws = NULL;
+    if (cudaMalloc(&ws, bytes) != cudaSuccess) return 40;
+    pmf_server *s = NULL;
+    CHECK(pmf_server_create(&d, ws, bytes, &s));
+    CHECK(pmf_server_start(s, 60.0));
+    const int32_t *a = p.arr;
+    CHECK(pmf_server_load(s, 2, 2, p.H, p.W, a, a + n, a + 2 * n, a + 3 * n, a + 4 * n, p.lam, p.m));
+    CHECK(pmf_server_load(s, 0, 2, p.H, p.W, NULL, NULL, a + 2 * n, a + 3 * n, a + 4 * n, p.lam, p.m));
+    const int32_t slots[2] = {2, 0};
+    CHECK(pmf_server_post(s, slots, 2));
+    for (long spin = 0;; ++spin) {
+        uint8_t done[3] = {0, 0, 0};
+        int32_t n_done = 0;
+        CHECK(pmf_server_poll(s, done, &n_done));
+        if (done[0] && done[2] && n_done == 2) break;
+        if (spin > 200000000L) return 41;
+    }
+    int64_t *flows = malloc(8 * (size_t)p.m), *flows2 = malloc(8 * (size_t)p.m);
+    uint8_t *masks = malloc(n * (size_t)p.m), *masks2 = malloc(n * (size_t)p.m);
+    if (!flows || !flows2 || !masks || !masks2) return 42;
+    CHECK(pmf_server_read(s, 0, masks, flows));
+    CHECK(pmf_server_read(s, 2, masks2, flows2));
+    if (memcmp(flows, flows2, 8 * (size_t)p.m) != 0 || memcmp(masks, masks2, n * (size_t)p.m) != 0) return 43;
+    if (pmf_server_read(s, 2, masks2, flows2) != PMF_ERR_NOT_READY) return 44;   /* read once */
+    CHECK(pmf_server_stop(s));
+    pmf_server_destroy(s);
+    cudaFree(ws);
+    rc = write_result(out_path, flows, masks, p.m, n);
+    free(p.lam); free(p.arr); free(flows); free(flows2); free(masks); free(masks2);
+    if (!rc) printf("server ok\n");
+    return rc;
+}
+
 int main(int argc, char **argv) {
     if (argc >= 2 && strcmp(argv[1], "host") == 0) return host_calls();
     if (argc >= 4 && strcmp(argv[1], "solve") == 0) return solve(argv[2], argv[3]);
     if (argc >= 4 && strcmp(argv[1], "noalloc") == 0) return solve_noalloc(argv[2], argv[3]);
-    fprintf(stderr, "usage: abi_client host | solve IN OUT | noalloc IN OUT\n");
+    if (argc >= 4 && strcmp(argv[1], "server") == 0) return solve_server(argv[2], argv[3]);
+    fprintf(stderr, "usage: abi_client host | solve IN OUT | noalloc IN OUT | server IN OUT\n");
     return 64;
 }

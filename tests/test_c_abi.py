@@ -83,7 +83,7 @@ def problem(H, W, seed):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("mode", ["solve", "noalloc"])
+@pytest.mark.parametrize("mode", ["solve", "noalloc", "server"])
 @pytest.mark.parametrize("shape", [(37, 45), (70, 90)])
 def test_solve_from_c_matches_oracle(client, tmp_path, mode, shape):
     import torch
