@@ -231,3 +231,63 @@ def test_gpu_exact_breakpoints(case):
     assert res.breakpoints == ref.breakpoints and all(res.verified)
     assert np.array_equal(res.masks, ref.masks) and np.array_equal(res.lines, ref.lines)
     assert (res.flow_lo, res.flow_hi) == (ref.flow_lo, ref.flow_hi)
+
+
+def _restricted(w_h, w_v, src0, slope, sink, s1, s2, p, q):
+    """The problem between two nested cuts as pmf_restrict_between documents it,
+    written independently here: pixels of D = s2 minus s1 keep their pairs to
+    each other, a pixel's pairs into s1 join its source capacity and its pairs
+    out of s2 its sink capacity, all capacities times q at lambda = p/q; every
+    other pixel gets no arcs and a unit sink capacity."""
+    i64 = lambda a: np.asarray(a, np.int64)
+    w_h, w_v, src0, slope, sink = map(i64, (w_h, w_v, src0, slope, sink))
+    H, W = w_h.shape
+    S1, S2 = np.asarray(s1) != 0, np.asarray(s2) != 0
+    D = S2 & ~S1
+    cs = np.zeros((H, W), np.int64)
+    ct = np.ones((H, W), np.int64)
+    wr = np.zeros((H, W), np.int64)
+    wd = np.zeros((H, W), np.int64)
+    for y in range(H):
+        for x in range(W):
+            if not D[y, x]:
+                continue
+            pin, pout = 0, 0
+            for (yy, xx, w) in ((y, x + 1, w_h[y, x] if x + 1 < W else 0), (y, x - 1, w_h[y, x - 1] if x > 0 else 0),
+                                (y + 1, x, w_v[y, x] if y + 1 < H else 0), (y - 1, x, w_v[y - 1, x] if y > 0 else 0)):
+                if not (0 <= yy < H and 0 <= xx < W):
+                    continue
+                if S1[yy, xx]:
+                    pin += w
+                elif not S2[yy, xx]:
+                    pout += w
+            cs[y, x] = q * (src0[y, x] + pin) + p * slope[y, x]
+            ct[y, x] = q * (sink[y, x] + pout)
+            if x + 1 < W and D[y, x + 1]:
+                wr[y, x] = q * w_h[y, x]
+            if y + 1 < H and D[y + 1, x]:
+                wd[y, x] = q * w_v[y, x]
+    return wr, wd, cs, ct
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_restricted_problem_decomposition(seed):
+    """Between the maximal cuts S1 at lambda_1 and S2 at lambda_2, the problem
+    restricted to S2 minus S1 and scaled at any rational lambda* in between
+    has the full problem's maximal cut at lambda* (joined with S1), and the
+    gap between the sum of its source capacities and its flow is q times the
+    gap between S1's line and F(lambda*) (Section 2's cut cost; the oracle
+    solves both problems)."""
+    from fractions import Fraction
+    H, W = 10, 12
+    args = _instance(H, W, 40 + seed)
+    f, m = oracle.grid_solve(H, W, *args, [30, 900])
+    s1, s2 = m[0], m[1]
+    a1, b1 = oracle.cut_line(H, W, *args, s1)
+    for lam in (Fraction(61, 2), Fraction(400, 3), Fraction(899, 1), Fraction(2137, 7)):
+        p, q = lam.numerator, lam.denominator
+        wr, wd, cs, ct = _restricted(*args, s1, s2, p, q)
+        sub_f, sub_m = oracle.grid_solve(H, W, wr, wd, cs, np.zeros_like(cs), ct, [0])
+        qf, full_m = oracle.grid_solve_rational(H, W, *args, p, q)
+        assert np.array_equal((sub_m[0] != 0) | (s1 != 0), full_m != 0)
+        assert int(cs.sum()) - int(sub_f[0]) == q * a1 + p * b1 - qf

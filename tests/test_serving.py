@@ -257,3 +257,88 @@ def test_lone_request_gets_the_whole_gpu():
     st = [serving.serve([req], slots=1, budget_bytes=4 << 30, realtime=False) for _ in range(3)]
     live = float(np.median([s.completed[0].latency_s for s in st]))
     assert live < 1.5 * alone + 0.02, (live, alone)
+
+
+@pytest.mark.gpu
+def test_c5_stream_on_the_live_server_against_oracle():
+    """The serving workload's own stream (Poisson arrivals at 50 requests/s,
+    images up to 800x600, 4-32 seeds, 10-30 lambdas; its first 12 requests,
+    which arrive within 0.3 s and so run mixed on the live server): every seed
+    of every request equals solving that request alone in one batch launch,
+    and the first seed of every request equals the oracle at every lambda
+    (Section 2's exact cut: flows and maximal source sets)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1509_06004_b300 import build, pmf
+    build.build()
+    reqs = inputs.serving_stream(50.0, 12, seed=0, max_side=800)
+    st = serving.serve(reqs, slots=16, budget_bytes=16 << 30, realtime=True, collect=True)
+    assert st.max_concurrent >= 4
+    for c, r in zip(st.completed, reqs):
+        wl = r.workload
+        status, alone = pmf.solve_workload(wl, tile_h=4, push_order=1, label_slack=8)
+        assert all(s == pmf.PMF_OK for s in status)
+        for (fa, ma), f, m in zip(alone, c.flows, c.masks):
+            assert np.array_equal(fa, f) and np.array_equal(ma, m)
+        (of, om), = oracle.solve_workload(wl, instances=[0])
+        assert np.array_equal(c.flows[0], of)
+        assert np.array_equal(c.masks[0], om)
+
+
+class FakeServer:
+    """Stands in for pmf.Server: slots finish when the test says so."""
+
+    def __init__(self, n):
+        self.n, self.loaded, self.posted, self.finished, self.images = n, set(), set(), set(), {}
+
+    def load(self, slot, image_slot, w_h, w_v, src0, slope, sink, lambdas):
+        assert slot not in self.posted
+        assert (w_h is not None) == (slot == image_slot)
+        self.loaded.add(slot)
+        self.images[slot] = image_slot
+
+    def post(self, slots):
+        assert all(s in self.loaded for s in slots)
+        self.posted.update(slots)
+
+    def poll(self):
+        return np.array([s in self.finished for s in range(self.n)])
+
+    def read(self, slot, check=True):
+        assert slot in self.finished
+        self.finished.discard(slot)
+        self.posted.discard(slot)
+        self.loaded.discard(slot)
+        return 0, np.zeros(1, np.int64), np.zeros((1, 1, 1), np.uint8)
+
+
+def test_live_backend_slot_bookkeeping():
+    """Each seed of a request takes a free slot, the first one holding the
+    image and the others using it; a request waits for enough free slots;
+    it is done when all its slots are; reading frees them."""
+    be = serving.LiveBackend.__new__(serving.LiveBackend)
+    from paper_1509_06004_b300 import pmf
+    be.pmf, be.server, be.n_slots, be.slot_bytes = pmf, FakeServer(5), 5, 100
+    be.free = list(range(5))[::-1]
+    reqs = inputs.serving_stream(rate_per_s=100.0, n_requests=3, seed=4, max_side=200)
+    for r, k in zip(reqs, (3, 2, 4)):
+        r.workload.instances = r.workload.instances[:k]
+    t0 = be.reserve(reqs[0])
+    t1 = be.reserve(reqs[1])
+    assert sorted(t0 + t1) == [0, 1, 2, 3, 4] and be.in_use() == 500
+    assert be.reserve(reqs[2]) is None                   # 4 seeds, no slot free
+    h0 = be.start(reqs[0], 0, t0)
+    assert all(be.server.images[s] == t0[0] for s in t0)
+    assert not be.done(h0)
+    be.server.finished.update(t0[:2])
+    assert not be.done(h0)
+    be.server.finished.update(t0)
+    assert be.done(h0)
+    be.finish(h0, collect=True)
+    be.release(t0)
+    assert be.bytes(reqs[2]) == 400 and be.reserve(reqs[2]) is None   # 3 free, 4 needed
+    be.release(t1)
+    t2 = be.reserve(reqs[2])
+    assert len(t2) == 4 and len(set(t2)) == 4
