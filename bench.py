@@ -223,7 +223,7 @@ def run_ours(args, rank, world, dev):
     tuning0 = {k: v for k, v in (("tile_h", args.tile_h), ("sweeps", args.sweeps),
                                  ("relabel_every", args.relabel_every), ("label_slack", args.label_slack),
                                  ("push_order", args.push_order), ("relabel_extra", args.relabel_extra),
-                                 ("poll_ns", args.poll_ns)) if v}
+                                 ("poll_ns", args.poll_ns), ("blocks_per_sm", args.blocks_per_sm)) if v}
     from paper_1509_06004_b300 import autotune
     m = min(len(i.lambdas) for i in wl.instances)
     plan, tuning, mode_probe = resolve_mode(args, wl, dev, tuning0)
@@ -302,7 +302,7 @@ def run_ours(args, rank, world, dev):
                        instances_launched=len(wl.instances),
                        sweeps=b.tuning()["sweeps"], relabel_every_pct=b.tuning()["relabel_every"],
                        relabel_extra=b.tuning()["relabel_extra"], poll_ns=b.tuning()["poll_ns"],
-                       label_slack=b.tuning()["label_slack"],
+                       label_slack=b.tuning()["label_slack"], blocks_per_sm=b.tuning()["blocks_per_sm"] or "occupancy",
                        l2="flushed between timed steps (512 MB write)",
                        parallelism=f"replicas x{world} (independent instances, no collective)"),
         "solves_per_s": solves_s,
@@ -628,6 +628,7 @@ def main(argv=None):
     ap.add_argument("--relabel-every", type=int, default=0)
     ap.add_argument("--relabel-extra", type=int, default=0)
     ap.add_argument("--poll-ns", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--label-slack", type=int, default=0)
     ap.add_argument("--push-order", type=int, default=0)
     ap.add_argument("--per-solve-sample", type=int, default=10)

@@ -100,7 +100,10 @@ typedef struct {
     int32_t mode;            /* 0 = one persistent launch fed by the device queue
                                 (default); 1 = host-polled rounds, one launch per
                                 round (the per-solve-launch baseline) */
-    int32_t blocks_per_sm;   /* persistent grid = blocks_per_sm * SMs; default: occupancy */
+    int32_t blocks_per_sm;   /* persistent grid = blocks_per_sm * SMs; default: occupancy
+                                (4 at tile height 4).  At tile height 4, 1-3 run a build
+                                compiled for 3 resident blocks, with more registers per
+                                thread and no spills (faster chains, fewer warps) */
     int32_t use_graph;       /* 1 = replay the solve as a captured CUDA graph (default 1;
                                 ignored in mode 1) */
     int32_t trace;           /* 1 = record instance phase changes (pmf_get_trace) */

@@ -19,8 +19,9 @@ instance count and schedule length:
   state, or along columns and rows), ``sweeps`` (push/relabel sweeps per tile visit),
   ``relabel_every`` (visit budget of a push/relabel phase, percent of its
   tiles), ``relabel_extra`` (visits added to every phase's budget),
-  ``label_slack`` (parking threshold above the last exact distance) and
-  ``poll_ns`` (longest sleep of an idle warp between polls of its queue slot).
+  ``label_slack`` (parking threshold above the last exact distance),
+  ``poll_ns`` (longest sleep of an idle warp between polls of its queue slot) and
+  ``blocks_per_sm`` (4 resident blocks, or 3 with more registers each).
 
 ``tune`` times candidates on the GPU by coordinate descent inside a time
 budget; choices are cached in a JSON file keyed by (GPU name, workload class).
@@ -39,7 +40,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_PATH = os.path.join(HERE, "tuned.json")
 
 DEFAULTS = {"tile_h": 4, "sweeps": 8, "relabel_every": 800, "label_slack": 16, "push_order": 0, "relabel_extra": 0,
-            "poll_ns": 256}
+            "poll_ns": 256, "blocks_per_sm": 0}
 SPACE = {
     "tile_h": [4, 8],
     "push_order": [0, 1],
@@ -48,6 +49,9 @@ SPACE = {
     "label_slack": [2, 4, 8, 16, 32],
     "relabel_extra": [0, 64, 256, 1024],
     "poll_ns": [256, 1024, 4096],
+    # 0: the occupancy (4 blocks per SM at tile height 4); 3: the build with
+    # the fourth block's registers (no spills)
+    "blocks_per_sm": [0, 3],
 }
 
 

@@ -708,6 +708,10 @@ static pmf_status solve_impl(pmf_batch *b, const int32_t *lambdas, const int32_t
         b->graph_valid = false;
     }
     b->worker_grid = grid_size(b);
+    // grids of 1-3 blocks per SM at tile height 4 run the build that spends
+    // the registers the fourth block would have had (no spills)
+    b->P.wide_regs = (b->tune.tile_h == 4 && b->tune.grid_blocks <= 0 && b->tune.blocks_per_sm >= 1 &&
+                      b->tune.blocks_per_sm <= 3) ? 1 : 0;
     b->solved = false;
     cudaError_t e = cudaSuccess;
     if (b->tune.mode == 1) {

@@ -168,6 +168,7 @@ struct Params {
     int32_t relabel_pct, tile_h;
     int32_t relabel_extra;       // visits added to every phase's budget
     int32_t any_sink_side;       // some instance's sink capacities fall with lambda (slope_side 1)
+    int32_t wide_regs;           // tile height 4 on 1-3 blocks per SM: the build with more registers
     int32_t poll_ns, label_slack;
     long long max_visits_per_tile;
     long long stall_ns;          // a worker gives up after this long without progress

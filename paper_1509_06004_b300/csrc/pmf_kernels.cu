@@ -1688,13 +1688,16 @@ __device__ int ring_pop_server(const Params &P, unsigned long long &ticket) {   
 // --------------------------------------------------------------------------
 constexpr int WORKER_WARPS = 4;
 
-template <int TH, int PO, bool SINK, bool SV>
-// at least 4 resident blocks per SM at tile height 4 (128 registers) and 2 at
-// height 8: with fewer, throughput-bound batches lose more than the spills cost.
+// MINB resident blocks per SM the register allocation must allow: 4 at tile
+// height 4 (128 registers) and 2 at height 8 by default (with fewer,
+// throughput-bound batches lose more than the spills cost); a second build at
+// tile height 4 for 3 blocks (up to 168 registers, no spills) serves grids of
+// 1 to 3 blocks per SM, where chains of dependent visits bound the launch.
 // SINK: the batch holds instances whose sink capacities fall with lambda
 // (their own kernels, so that the others' register allocation is untouched).
 // SV: the server kernel (instances admitted from the mailbox while it runs)
-__global__ void __launch_bounds__(WORKER_WARPS * 32, TH == 4 ? 4 : 2) worker_kernel(const __grid_constant__ Params P) {
+template <int TH, int PO, bool SINK, bool SV, int MINB = (TH == 4 ? 4 : 2)>
+__global__ void __launch_bounds__(WORKER_WARPS * 32, MINB) worker_kernel(const __grid_constant__ Params P) {
     __shared__ WarpSmem<TH> smem[WORKER_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<TH> &S = smem[w];
@@ -2150,6 +2153,9 @@ cudaError_t launch_worker(const Params &P, int grid, cudaStream_t s) {
             if (P.chain_push) worker_kernel<8, 1, true, false><<<grid, b, 0, s>>>(P);
             else worker_kernel<8, 0, true, false><<<grid, b, 0, s>>>(P);
         }
+    } else if (P.tile_h == 4 && P.wide_regs) {
+        if (P.chain_push) worker_kernel<4, 1, false, false, 3><<<grid, b, 0, s>>>(P);
+        else worker_kernel<4, 0, false, false, 3><<<grid, b, 0, s>>>(P);
     } else if (P.tile_h == 4) {
         if (P.chain_push) worker_kernel<4, 1, false, false><<<grid, b, 0, s>>>(P);
         else worker_kernel<4, 0, false, false><<<grid, b, 0, s>>>(P);
