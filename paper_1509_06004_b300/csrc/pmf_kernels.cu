@@ -713,6 +713,18 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
                 e[i] -= dT;
                 rt[i] -= dT;
             }
+            // the sweeps alternate: even ones push down the columns and
+            // rightwards along the rows, odd ones up and leftwards.  A sweep
+            // is a chain of dependent steps (its rows are the only
+            // independent work), so half the steps make each sweep about
+            // half as long, and over two sweeps excess still moves every way.
+            // The last sweep of a visit with an odd number of sweeps goes
+            // every way, so that each visit offers every admissible arc a push
+            // (a pixel whose only admissible arcs lead up or left must not
+            // wait for a sweep that never comes).
+            const bool even = (sw & 1) == 0;
+            const bool full = (P.sweeps & 1) && sw == P.sweeps - 1;
+            if (even || full) {
 #pragma unroll
             for (int i = 0; i < TH; ++i) {             // down the column, top to bottom
                 const int hD = (i < TH - 1) ? h[i + 1] : hB;
@@ -723,6 +735,8 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
                 fd[i] += d;
                 if (i < TH - 1) e[i + 1] += d; else outD += d;
             }
+            }
+            if (!even || full) {
 #pragma unroll
             for (int i = TH - 1; i >= 0; --i) {        // up the column, bottom to top
                 const int hU = (i > 0) ? h[i - 1] : hT;
@@ -731,6 +745,7 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
                 const int d = (a && rU > 0 && hU < h[i]) ? min(e[i], rU) : 0;
                 e[i] -= d;
                 if (i > 0) { e[i - 1] += d; fd[i - 1] -= d; } else { outU += d; fdT -= d; }
+            }
             }
             // along the row: a pixel forwards min(its excess + what arrives
             // from the previous pixel of the run, residual of its arc) when
@@ -742,7 +757,7 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
             constexpr int ACL = 1 << 29;
             // all rows scan in step (independent shuffles overlap); a direction
             // is skipped when no pixel of the tile can send anything along it
-            {                                          // rightwards
+            if (even || full) {                        // rightwards
                 int A[TH], B[TH];
                 bool go = false;
 #pragma unroll
@@ -776,7 +791,7 @@ __device__ void pr_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, cons
                     }
                 }
             }
-            {                                          // leftwards
+            if (!even || full) {                       // leftwards
                 int A[TH], B[TH];
                 bool go = false;
 #pragma unroll

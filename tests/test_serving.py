@@ -233,8 +233,9 @@ def test_server_slots_bad_inputs_and_reuse():
 @pytest.mark.gpu
 def test_lone_request_gets_the_whole_gpu():
     """A lone request on the live server takes about as long as solving it
-    alone in one batch launch (no static share of the SMs), within a margin
-    for the admission path."""
+    alone end to end in one batch launch that has the whole GPU (host inputs
+    uploaded, solve, every mask and flow read back), within a margin for the
+    admission path: no static share of the SMs holds it back."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -244,13 +245,20 @@ def test_lone_request_gets_the_whole_gpu():
     req = inputs.serving_stream(rate_per_s=10.0, n_requests=1, seed=11, max_side=640)[0]
     req.arrival_s = 0.0
     wl = req.workload
+    im = wl.images[0]
     b = pmf.batch_from_workload(wl, tile_h=4, push_order=1, label_slack=8)
     lam = np.stack([i.lambdas for i in wl.instances])
     ts = []
     for _ in range(4):
         t0 = time.perf_counter()
+        b.set_capacities(0, im.w_h, im.w_v)
+        for i, inst in enumerate(wl.instances):
+            b.set_terminals(i, inst.src0, inst.slope, inst.sink)
         b.solve(lam)
         b.sync()
+        for i in range(len(wl.instances)):
+            b.flows(i)
+            b.cuts(i)
         ts.append(time.perf_counter() - t0)
     b.close()
     alone = float(np.median(ts[1:]))
