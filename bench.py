@@ -200,13 +200,21 @@ def resolve_mode(args, wl, dev, tuning0):
     from paper_1509_06004_b300 import autotune
     m = min(len(i.lambdas) for i in wl.instances)
     plan = parse_mode(args.mode, m)
-    if plan is not None:
-        return plan, tuning0, None
     c = autotune.cached(wl, dev.index)
-    if c is not None and not tuning0:
+    if plan is not None:
+        # an explicit batching runs with the class's tuned knobs, if any, and
+        # the knobs given on the command line
+        if c is None:
+            return plan, tuning0, None
+        return plan, {**autotune.knobs_of(autotune.bench_plan(wl, dev.index)), **tuning0}, \
+            {"source": "explicit mode, autotune cache knobs", "class": autotune.workload_class(wl)}
+    if c is not None:
+        # knobs given on the command line replace the cached ones
         p = autotune.bench_plan(wl, dev.index)
-        return ({"segments": p["segments"], "interleave": p["interleave"], "fork": p["fork"]}, autotune.knobs_of(p),
-                {"source": "autotune cache", "class": autotune.workload_class(wl), "tuned_ms": c.get("ms")})
+        return ({"segments": p["segments"], "interleave": p["interleave"], "fork": p["fork"]},
+                {**autotune.knobs_of(p), **tuning0},
+                {"source": "autotune cache" + (" with " + ", ".join(sorted(tuning0)) + " set" if tuning0 else ""),
+                 "class": autotune.workload_class(wl), "tuned_ms": c.get("ms")})
     divs = autotune.divisors(m)
     cands = sorted({1, divs[len(divs) // 2], m})
     probe = {s: quick_rate(wl.split_segments(s) if s > 1 else wl, dev, tuning0) for s in cands}
@@ -223,7 +231,8 @@ def run_ours(args, rank, world, dev):
     tuning0 = {k: v for k, v in (("tile_h", args.tile_h), ("sweeps", args.sweeps),
                                  ("relabel_every", args.relabel_every), ("label_slack", args.label_slack),
                                  ("push_order", args.push_order), ("relabel_extra", args.relabel_extra),
-                                 ("poll_ns", args.poll_ns), ("blocks_per_sm", args.blocks_per_sm)) if v}
+                                 ("poll_ns", args.poll_ns), ("blocks_per_sm", args.blocks_per_sm),
+                                 ("strip_stage", args.strip_stage)) if v}
     from paper_1509_06004_b300 import autotune
     m = min(len(i.lambdas) for i in wl.instances)
     plan, tuning, mode_probe = resolve_mode(args, wl, dev, tuning0)
@@ -303,6 +312,7 @@ def run_ours(args, rank, world, dev):
                        sweeps=b.tuning()["sweeps"], relabel_every_pct=b.tuning()["relabel_every"],
                        relabel_extra=b.tuning()["relabel_extra"], poll_ns=b.tuning()["poll_ns"],
                        label_slack=b.tuning()["label_slack"], blocks_per_sm=b.tuning()["blocks_per_sm"] or "occupancy",
+                       strip_loads="tensor copies" if b.tuning()["strip_stage"] == 1 else "per lane",
                        l2="flushed between timed steps (512 MB write)",
                        parallelism=f"replicas x{world} (independent instances, no collective)"),
         "solves_per_s": solves_s,
@@ -630,6 +640,8 @@ def main(argv=None):
     ap.add_argument("--poll-ns", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--label-slack", type=int, default=0)
+    ap.add_argument("--strip-stage", type=int, default=0,
+                    help="1: relabel strips' first visits load through tensor copies; -1: per-lane loads")
     ap.add_argument("--push-order", type=int, default=0)
     ap.add_argument("--per-solve-sample", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

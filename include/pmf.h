@@ -121,6 +121,11 @@ typedef struct {
     int32_t relabel_extra;   /* tile visits every push/relabel phase may spend on top
                                 of relabel_every% of its tiles (default 0): more room
                                 for phases that start with few active tiles */
+    int32_t strip_stage;     /* 1 = a relabel strip's first visit of a global relabel
+                                loads its 32 rows of state and capacities with two
+                                tensor copies into shared memory (one buffer per
+                                block) instead of per-lane loads; -1 or 0 = per-lane
+                                loads (default) */
 } pmf_tuning;
 
 /* One instance phase change recorded on the device (tuning.trace = 1). */

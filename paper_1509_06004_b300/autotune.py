@@ -40,7 +40,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_PATH = os.path.join(HERE, "tuned.json")
 
 DEFAULTS = {"tile_h": 4, "sweeps": 8, "relabel_every": 800, "label_slack": 16, "push_order": 0, "relabel_extra": 0,
-            "poll_ns": 256, "blocks_per_sm": 0}
+            "poll_ns": 256, "blocks_per_sm": 0, "strip_stage": -1}
 SPACE = {
     "tile_h": [4, 8],
     "push_order": [0, 1],

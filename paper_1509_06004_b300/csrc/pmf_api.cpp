@@ -29,7 +29,7 @@ int round_up_i(int v, int a) { return (v + a - 1) / a * a; }
 
 struct Layout {
     size_t img_planes, inst_planes, masks, dev_inst, ist, tiles, tile_inst, ring, lambdas, flows,
-        globals, staging, img_flags, inst_flags, scratch, trace, strip_cache, total;
+        globals, staging, img_flags, inst_flags, scratch, trace, strip_cache, tmaps, total;
     size_t ring_cap;
     size_t max_tiles;
     size_t max_strips;                          // relabel strips (tile columns x 32-row bands)
@@ -100,6 +100,7 @@ Layout make_layout(const pmf_batch_desc *d) {
     L.scratch = take(256);                        // small device results (status words)
     L.trace = take(sizeof(TraceEvent) * TRACE_CAP);
     L.strip_cache = take(sizeof(int32_t) * STRIP_REC_WORDS * L.max_strips);
+    L.tmaps = take((size_t)TMAP_BYTES * (d->n_inst + d->n_images));
     L.total = off;
     return L;
 }
@@ -215,6 +216,7 @@ struct pmf_batch {
     cudaGraphExec_t gexec = nullptr;
     bool graph_valid = false;
     int worker_grid = 0;
+    bool stage_ok = false;                 // tensor maps encoded: staged strip loads available
 };
 
 namespace pmf {
@@ -246,6 +248,7 @@ void apply_defaults(pmf_tuning *t) {
     if (t->label_slack < 0) t->label_slack = -1;
     if (t->push_order != 1) t->push_order = 0;
     if (t->relabel_extra < 0) t->relabel_extra = 0;
+    if (t->strip_stage != 1) t->strip_stage = -1;
 }
 
 // per-instance tile geometry for the current tile height; uploads the table
@@ -304,7 +307,7 @@ int grid_size(pmf_batch *b) {
     if (b->tune.grid_blocks > 0) return b->tune.grid_blocks;
     int bps = b->tune.blocks_per_sm;
     if (bps <= 0) {
-        if (worker_occupancy(b->tune.tile_h, &bps) != cudaSuccess || bps <= 0) bps = 4;
+        if (worker_occupancy(b->tune.tile_h, &bps, b->P.strip_stage != 0) != cudaSuccess || bps <= 0) bps = 4;
     }
     return bps * b->n_sm;
 }
@@ -459,6 +462,19 @@ pmf_status pmf_create_batch(const pmf_batch_desc *desc, void *dev_workspace, siz
         const pmf_status st = refresh_geometry(b, s);
         if (st != PMF_OK) e = cudaErrorUnknown;
     }
+    // tensor maps of the planes for staged strip loads (the workspace does not
+    // move for the batch's lifetime); without an encoder the loads stay per lane
+    std::vector<unsigned char> maps((size_t)TMAP_BYTES * (desc->n_inst + desc->n_images));
+    if (e == cudaSuccess) {
+        std::vector<int> rows(L.rows.begin(), L.rows.end()), pitch(L.pitch.begin(), L.pitch.end());
+        b->stage_ok = encode_plane_maps(maps.data(), P.planes, P.img, desc->n_inst, L.plane_off.data(),
+                                        b->inst_image.data(), desc->n_images, L.img_off.data(), rows.data(),
+                                        pitch.data()) &&
+                      prepare_stage_kernels() == cudaSuccess;
+        (void)cudaGetLastError();
+        if (b->stage_ok) e = cudaMemcpyAsync(b->ws + L.tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice, s);
+    }
+    P.tmaps = (const unsigned char *)(b->ws + L.tmaps);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         pmf_destroy_batch(b);
@@ -699,6 +715,7 @@ static pmf_status solve_impl(pmf_batch *b, const int32_t *lambdas, const int32_t
     b->P.any_sink_side = 0;
     for (int i = 0; i < b->desc.n_inst; ++i) b->P.any_sink_side |= b->dinst[i].slope_side != 0;
     b->P.max_visits_per_tile = b->tune.max_visits_per_tile;
+    b->P.strip_stage = (b->tune.strip_stage == 1 && b->stage_ok) ? 1 : 0;
     const bool geo_changed = (b->P.tile_h != b->tune.tile_h) || len_changed || b->forks_changed;
     if (geo_changed) {
         // tile geometry and schedule lengths live in the descriptor table

@@ -24,6 +24,16 @@ constexpr int STRIP_REC_WORDS = (RW_CNT + 1) * 32;
 constexpr int N_INST_PLANES = 8;           // e, h, rt, fR, fD, src0, slope, ct
 constexpr int N_IMG_PLANES = 2;            // w_h, w_v
 enum Plane { P_E = 0, P_H = 1, P_RT = 2, P_FR = 3, P_FD = 4, P_SRC0 = 5, P_SLOPE = 6, P_CT = 7 };
+// Tensor-memory-access staging of a relabel strip's first visit: one box of the
+// instance's planes e, h, rt, fR, fD (consecutive, so one 3-D copy) and one of
+// the image's w_h, w_v, each 32 rows x STAGE_BOX_W columns starting at the
+// strip's first column rounded down to a multiple of 4 (a copy's innermost
+// coordinate must be 16-byte aligned)
+constexpr int STAGE_BOX_W = 36;
+constexpr int STAGE_INST_PLANES = 5;
+constexpr int STAGE_WORDS = (STAGE_INST_PLANES + N_IMG_PLANES) * BFS_ROWS * STAGE_BOX_W;
+constexpr int STAGE_BYTES = STAGE_WORDS * 4;
+constexpr int TMAP_BYTES = 128;            // one CUtensorMap
 
 // instance phases
 // PH_FWD: after a certified step of an instance whose caller swapped s and t,
@@ -42,8 +52,8 @@ enum Phase { PH_BFS = 0, PH_PR = 1, PH_DONE = 2, PH_FWD = 3, PH_WARM = 4, PH_COP
 enum TState { T_IDLE = 0, T_QUEUED = 1, T_RUNNING = 2, T_DIRTY = 3 };
 // global error flags; GE_INTERNAL_MASK marks a broken scheduler invariant, after
 // which no instance's result is trusted
-enum GErr { GE_STALL = 1, GE_RING = 2, GE_SLOT = 4, GE_TIMEOUT = 8, GE_PHASE = 16 };
-constexpr int GE_INTERNAL_MASK = GE_RING | GE_PHASE;
+enum GErr { GE_STALL = 1, GE_RING = 2, GE_SLOT = 4, GE_TIMEOUT = 8, GE_PHASE = 16, GE_STAGE = 32 };
+constexpr int GE_INTERNAL_MASK = GE_RING | GE_PHASE | GE_STAGE;
 // per-instance validation flags (set by the pad/init kernels)
 enum VFlag { VF_NEG = 1, VF_OVERFLOW = 2, VF_SLOPE = 4, VF_BADCAP = 8 };
 
@@ -170,6 +180,10 @@ struct Params {
     int32_t any_sink_side;       // some instance's sink capacities fall with lambda (slope_side 1)
     int32_t wide_regs;           // tile height 4 on 1-3 blocks per SM: the build with more registers
     int32_t poll_ns, label_slack;
+    // tensor maps for staged relabel-strip loads: [n_inst] instance planes, then
+    // [n_images] image planes (TMAP_BYTES each, device memory), or nullptr
+    const unsigned char *tmaps;
+    int32_t strip_stage;         // 1: first relabel visits load through tmaps (dynamic shared memory)
     long long max_visits_per_tile;
     long long stall_ns;          // a worker gives up after this long without progress
     long long max_ns;            // ... or after this long in one launch
@@ -196,6 +210,13 @@ int worker_warps_per_block();
 // records "where: <CUDA error text>" for pmf_last_error (this thread) and
 // returns PMF_ERR_CUDA; PMF_OK for cudaSuccess
 pmf_status cuda_err_at(cudaError_t e, const char *where);
-cudaError_t worker_occupancy(int tile_h, int *blocks_per_sm);
+cudaError_t worker_occupancy(int tile_h, int *blocks_per_sm, bool staged = false);
+// lets the batch kernels take the staging buffer's shared memory (once per process)
+cudaError_t prepare_stage_kernels();
+// device tensor maps of a batch's planes for staged strip loads (host side);
+// false when the driver offers no tensor-map encoder
+bool encode_plane_maps(unsigned char *host_out, const int32_t *inst_base, const int32_t *img_base,
+                       int n_inst, const int64_t *plane_off, const int *inst_image, int n_images,
+                       const int64_t *img_off, const int *rows, const int *pitch);
 
 }  // namespace pmf

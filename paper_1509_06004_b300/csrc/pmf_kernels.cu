@@ -39,6 +39,11 @@
 #include <cstdint>
 
 #include <cooperative_groups.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
 
 #include "pmf.h"
 #include "pmf_internal.h"
@@ -86,6 +91,97 @@ struct WarpSmem {
     int d[BFS_ROWS][33];    // relabel: the strip's labels, row i / column l (one pad column, so
                             // a lane walking a row and a lane walking a column both hit 32 banks)
 };
+
+// --------------------------------------------------------------------------
+// staged strip loads (batch kernels): a relabel strip's first visit of an
+// epoch reads seven planes over its 32 rows.  Instead of per-lane loads in
+// batches of a few rows (one memory round trip each), one elected lane starts
+// two tensor copies (the instance's e, h, rt, fR, fD box and the image's w_h,
+// w_v box) into a shared-memory buffer of the block, and the warp waits once on
+// an mbarrier for all of it.  One buffer per block: a warp that finds it taken
+// loads per lane as before.
+// --------------------------------------------------------------------------
+struct StripStage {
+    int32_t *buf;                   // [5 + 2 planes][BFS_ROWS][STAGE_BOX_W]
+    unsigned long long *bar;        // completion of the copies into buf
+    int *lock;                      // 0 free, 1 held by a warp of the block, 2 out of use
+    int *uses;                      // completed uses of buf (parity of the barrier's phase)
+};
+constexpr unsigned long long STAGE_WAIT_NS = 1000000000ULL;   // a copy not done by then is an error
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// block start (thread 0): the barrier expects one arrival per phase, plus the
+// copies' bytes
+__device__ __forceinline__ void stage_init(const StripStage &SS) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(SS.bar)) : "memory");
+    *SS.lock = 0;
+    *SS.uses = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void stage_copy(uint32_t dst, const unsigned char *tmap, int x, int y, int z,
+                                           uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+// lane 0: takes the buffer if it is free and starts the copies of the box whose
+// first column is x0 (a multiple of 4; may be negative: the copy fills zeros
+// outside the plane) and first row y0.  Returns the barrier parity to wait
+// for, or -1 when the buffer is taken.
+__device__ int stage_begin(const Params &P, const StripStage &SS, int inst, int image, int x0, int y0) {
+    if (atomicCAS(SS.lock, 0, 1) != 0) return -1;
+    __threadfence_block();
+    const int parity = *(volatile int *)SS.uses & 1;
+    const uint32_t bar = smem_addr(SS.bar);
+    // the planes were written through the generic proxy (by other warps, seen
+    // through this lane's acquires); the copies read through the async proxy
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(STAGE_BYTES) : "memory");
+    stage_copy(smem_addr(SS.buf), P.tmaps + (size_t)inst * TMAP_BYTES, x0, y0, P_E, bar);
+    stage_copy(smem_addr(SS.buf + STAGE_INST_PLANES * BFS_ROWS * STAGE_BOX_W),
+               P.tmaps + (size_t)(P.n_inst + image) * TMAP_BYTES, x0, y0, 0, bar);
+    return parity;
+}
+
+// whole warp: wait until every lane sees the copies done (the barrier's phase
+// of this parity complete); false after STAGE_WAIT_NS
+__device__ bool stage_wait(const StripStage &SS, int parity) {
+    const uint32_t bar = smem_addr(SS.bar);
+    unsigned long long t0 = 0;
+    for (int spin = 0;; ++spin) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (__all_sync(FULL_MASK, ok != 0)) return true;
+        unsigned long long now = gtime_ns();
+        now = __shfl_sync(FULL_MASK, now, 0);
+        if (t0 == 0) t0 = now;
+        else if (now - t0 > STAGE_WAIT_NS) return false;
+    }
+}
+
+// whole warp, after every lane has read the buffer: hand it back
+__device__ __forceinline__ void stage_end(const StripStage &SS) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        *(volatile int *)SS.uses = *(volatile int *)SS.uses + 1;
+        __threadfence_block();
+        atomicExch(SS.lock, 0);
+    }
+    __syncwarp();
+}
 
 // --------------------------------------------------------------------------
 // device work queue: ring of tile ids, ticket counters head/tail
@@ -1141,8 +1237,8 @@ __device__ __noinline__ void copy_visit(const Params &P, int g, int inst, const 
 // count of active pixels for the push/relabel phase that may follow.
 // --------------------------------------------------------------------------
 template <int TH, bool FWD, bool SV>
-__device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, const DevInst &D,
-                          int epoch, int kcur, bool &self_again, unsigned &nbmask) {
+__device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, const StripStage &SS, int g, int inst,
+                          const DevInst &D, int epoch, int kcur, bool &self_again, unsigned &nbmask) {
     constexpr int BR = BFS_ROWS;
     constexpr int SPAN = BR / TH;
     const TileGeo T = tile_geo(g, D, TH);
@@ -1247,6 +1343,25 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
             }
         }
     } else {
+    // staged loads: lane 0 starts the copies of the strip's box before the
+    // loads of the row above, so that both are in flight together.  The box
+    // starts at lane 0's column rounded down to a multiple of 4; lane l reads
+    // box column sx + l.  Lane 0 first acquires the right neighbour's epoch as
+    // well (lane 31 did, for the labels of its column that the copy brings in).
+    int parity = -1;
+    const int xl = T.tx * TILE_IN - 1;
+    const int x0 = xl - (((xl % 4) + 4) % 4);
+    const int sx = xl - x0;
+    if constexpr (!SV) {
+        if (P.strip_stage) {
+            __syncwarp();
+            if (lane == 0) {
+                if (T.tx < D.tiles_x - 1) (void)ld_acquire(&P.tiles[g + 1].epoch);
+                parity = stage_begin(P, SS, inst, D.image, x0, T.y0);
+            }
+            parity = __shfl_sync(FULL_MASK, parity, 0);
+        }
+    }
     // the row above the strip: residual of the arcs up and down across the border
     if (own && T.y0 > 0) {
         const size_t j = (size_t)(T.y0 - 1) * pitch + T.X;
@@ -1264,29 +1379,57 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
     // on its right (read by lane 1 from ghost lane 0); V = arc from the right
     // neighbour into this column (used by lane 30).  Labels live in this
     // lane's own column of the warp's shared memory.
+    bool staged = parity >= 0;
+    if (staged && !stage_wait(SS, parity)) {
+        // the copies did not finish in time: an error for the launch; wait once
+        // more for them, then either use the data or retire the buffer (a copy
+        // might still land in it) and load per lane
+        if (lane == 0) atomicOr(&P.g->err, GE_STAGE);
+        staged = stage_wait(SS, parity);
+        if (!staged && lane == 0) atomicExch(SS.lock, 2);
+    }
     int prev_up = res_up0;
     // 4 rows at a time: every global load of a batch is issued before any of
     // its results is used or written to shared memory, so a batch costs one
     // memory round trip instead of one per row
     constexpr int LB = 4;
+    constexpr int PW = BFS_ROWS * STAGE_BOX_W;     // words per staged plane
 #pragma unroll 1
     for (int c0 = 0; c0 < BR; c0 += LB) {
         int fr[LB], wh[LB], fd[LB], wv[LB], rt[LB], ev[LB], dv[LB];
+        if (staged) {
 #pragma unroll
-        for (int j = 0; j < LB; ++j) {
-            const int y = T.y0 + c0 + j;
-            const bool rowok = y < D.rows;
-            const size_t idx = (size_t)y * pitch + T.X;
-            const bool ldc = T.inb && rowok && lane != 31;
-            const bool ldo = own && rowok;
-            fr[j] = ldc ? __ldcg(FR + idx) : 0;
-            wh[j] = ldc ? ldro<SV>(WH + idx) : 0;
-            fd[j] = ldo ? __ldcg(FD + idx) : 0;
-            wv[j] = ldo ? ldro<SV>(WV + idx) : 0;
-            rt[j] = ldo ? __ldcg(RT + idx) : 0;
-            ev[j] = ldo ? __ldcg(E + idx) : 0;
-            if constexpr (FWD) dv[j] = (T.inb && rowok && vX) ? ghost_label(c0 + j) : HINF;
-            else dv[j] = (T.inb && rowok && vX) ? __ldcg(Hh + idx) : HINF;
+            for (int j = 0; j < LB; ++j) {
+                const bool rowok = T.y0 + c0 + j < D.rows;
+                const bool ldc = T.inb && rowok && lane != 31;
+                const bool ldo = own && rowok;
+                const int32_t *sb = SS.buf + (c0 + j) * STAGE_BOX_W + sx + lane;
+                fr[j] = ldc ? sb[(P_FR - P_E) * PW] : 0;
+                wh[j] = ldc ? sb[STAGE_INST_PLANES * PW] : 0;
+                fd[j] = ldo ? sb[(P_FD - P_E) * PW] : 0;
+                wv[j] = ldo ? sb[(STAGE_INST_PLANES + 1) * PW] : 0;
+                rt[j] = ldo ? sb[(P_RT - P_E) * PW] : 0;
+                ev[j] = ldo ? sb[0] : 0;
+                if constexpr (FWD) dv[j] = (T.inb && rowok && vX) ? ghost_label(c0 + j) : HINF;
+                else dv[j] = (T.inb && rowok && vX) ? sb[(P_H - P_E) * PW] : HINF;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < LB; ++j) {
+                const int y = T.y0 + c0 + j;
+                const bool rowok = y < D.rows;
+                const size_t idx = (size_t)y * pitch + T.X;
+                const bool ldc = T.inb && rowok && lane != 31;
+                const bool ldo = own && rowok;
+                fr[j] = ldc ? __ldcg(FR + idx) : 0;
+                wh[j] = ldc ? ldro<SV>(WH + idx) : 0;
+                fd[j] = ldo ? __ldcg(FD + idx) : 0;
+                wv[j] = ldo ? ldro<SV>(WV + idx) : 0;
+                rt[j] = ldo ? __ldcg(RT + idx) : 0;
+                ev[j] = ldo ? __ldcg(E + idx) : 0;
+                if constexpr (FWD) dv[j] = (T.inb && rowok && vX) ? ghost_label(c0 + j) : HINF;
+                else dv[j] = (T.inb && rowok && vX) ? __ldcg(Hh + idx) : HINF;
+            }
         }
 #pragma unroll
         for (int j = 0; j < LB; ++j) {
@@ -1313,6 +1456,7 @@ __device__ void bfs_visit(const Params &P, WarpSmem<TH> &S, int g, int inst, con
             if (lane == 30) S.dl0[1][i] = dv[j];
         }
     }
+    if (staged) stage_end(SS);
     // the record's masks and residuals for the epoch's later visits
     __stcg(REC + 0 * 32 + lane, (int)bR);
     __stcg(REC + 1 * 32 + lane, (int)bD);
@@ -1714,8 +1858,18 @@ constexpr int WORKER_WARPS = 4;
 template <int TH, int PO, bool SINK, bool SV, int MINB = (TH == 4 ? 4 : 2)>
 __global__ void __launch_bounds__(WORKER_WARPS * 32, MINB) worker_kernel(const __grid_constant__ Params P) {
     __shared__ WarpSmem<TH> smem[WORKER_WARPS];
+    // staged strip loads: the block's buffer (dynamic shared memory, present
+    // only when P.strip_stage is set) and its barrier
+    extern __shared__ __align__(128) int32_t stage_buf[];
+    __shared__ __align__(8) unsigned long long stage_bar;
+    __shared__ int stage_lock, stage_uses;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<TH> &S = smem[w];
+    const StripStage SS{stage_buf, &stage_bar, &stage_lock, &stage_uses};
+    if (!SV && P.strip_stage) {
+        if (threadIdx.x == 0) stage_init(SS);
+        __syncthreads();
+    }
     const int round_mode = ldv(&P.g->round_mode);
     const bool prof = P.trace != nullptr;
     unsigned long long tw = 0, tpr = 0, tbfs = 0, tfin = 0, t0 = prof ? gtime_ns() : 0;
@@ -1774,9 +1928,9 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, MINB) worker_kernel(const _
         if (stray && lane == 0) atomicOr(&P.g->err, GE_PHASE);
         if (status == PMF_OK && phase == PH_PR) pr_visit<TH, PO, SV>(P, S, g, inst, D, k, requeue, nb);
         else if (status == PMF_OK && phase == PH_BFS && !stray)
-            bfs_visit<TH, false, SV>(P, S, g, inst, D, epoch, k, requeue, nb);
+            bfs_visit<TH, false, SV>(P, S, SS, g, inst, D, epoch, k, requeue, nb);
         else if (status == PMF_OK && phase == PH_FWD && !stray)
-            bfs_visit<TH, true, SV>(P, S, g, inst, D, epoch, k, requeue, nb);
+            bfs_visit<TH, true, SV>(P, S, SS, g, inst, D, epoch, k, requeue, nb);
         else if (status == PMF_OK && phase == PH_WARM && !stray) warm_visit<TH, SINK, SV>(P, g, inst, D, k);
         else if (status == PMF_OK && phase == PH_COPY && !stray) copy_visit<TH, SV>(P, g, inst, D);
         else if (SV && phase == PH_SETUP && !stray) setup_visit<TH>(P, g, inst, D);
@@ -2156,29 +2310,53 @@ cudaError_t launch_return_excess(const Params &P, const DevInst &d, int lambda, 
                                        s);
 }
 
+// the batch kernels, by (any sink side, wide registers, tile height, push order)
+static const void *batch_worker(const Params &P) {
+    if (P.any_sink_side) {
+        if (P.tile_h == 4) return P.chain_push ? (const void *)worker_kernel<4, 1, true, false>
+                                               : (const void *)worker_kernel<4, 0, true, false>;
+        return P.chain_push ? (const void *)worker_kernel<8, 1, true, false>
+                            : (const void *)worker_kernel<8, 0, true, false>;
+    }
+    if (P.tile_h == 4 && P.wide_regs)
+        return P.chain_push ? (const void *)worker_kernel<4, 1, false, false, 3>
+                            : (const void *)worker_kernel<4, 0, false, false, 3>;
+    if (P.tile_h == 4)
+        return P.chain_push ? (const void *)worker_kernel<4, 1, false, false>
+                            : (const void *)worker_kernel<4, 0, false, false>;
+    return P.chain_push ? (const void *)worker_kernel<8, 1, false, false>
+                        : (const void *)worker_kernel<8, 0, false, false>;
+}
+
+cudaError_t prepare_stage_kernels() {
+    // static plus staging shared memory exceeds the 48 KB a kernel gets without
+    // asking; set once per process, outside any stream capture
+    static cudaError_t done = [] {
+        const void *ks[] = {(const void *)worker_kernel<4, 1, true, false>,
+                            (const void *)worker_kernel<4, 0, true, false>,
+                            (const void *)worker_kernel<8, 1, true, false>,
+                            (const void *)worker_kernel<8, 0, true, false>,
+                            (const void *)worker_kernel<4, 1, false, false, 3>,
+                            (const void *)worker_kernel<4, 0, false, false, 3>,
+                            (const void *)worker_kernel<4, 1, false, false>,
+                            (const void *)worker_kernel<4, 0, false, false>,
+                            (const void *)worker_kernel<8, 1, false, false>,
+                            (const void *)worker_kernel<8, 0, false, false>};
+        for (const void *k : ks) {
+            const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_BYTES);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }();
+    return done;
+}
+
 cudaError_t launch_worker(const Params &P, int grid, cudaStream_t s) {
     (void)cudaGetLastError();
     // one kernel per tile height and push order: each holds only the sweep it runs
-    const dim3 b(WORKER_WARPS * 32);
-    if (P.any_sink_side) {
-        if (P.tile_h == 4) {
-            if (P.chain_push) worker_kernel<4, 1, true, false><<<grid, b, 0, s>>>(P);
-            else worker_kernel<4, 0, true, false><<<grid, b, 0, s>>>(P);
-        } else {
-            if (P.chain_push) worker_kernel<8, 1, true, false><<<grid, b, 0, s>>>(P);
-            else worker_kernel<8, 0, true, false><<<grid, b, 0, s>>>(P);
-        }
-    } else if (P.tile_h == 4 && P.wide_regs) {
-        if (P.chain_push) worker_kernel<4, 1, false, false, 3><<<grid, b, 0, s>>>(P);
-        else worker_kernel<4, 0, false, false, 3><<<grid, b, 0, s>>>(P);
-    } else if (P.tile_h == 4) {
-        if (P.chain_push) worker_kernel<4, 1, false, false><<<grid, b, 0, s>>>(P);
-        else worker_kernel<4, 0, false, false><<<grid, b, 0, s>>>(P);
-    } else {
-        if (P.chain_push) worker_kernel<8, 1, false, false><<<grid, b, 0, s>>>(P);
-        else worker_kernel<8, 0, false, false><<<grid, b, 0, s>>>(P);
-    }
-    return cudaGetLastError();
+    const void *k = batch_worker(P);
+    void *args[] = {(void *)&P};
+    return cudaLaunchKernel(k, dim3(grid), dim3(WORKER_WARPS * 32), args, P.strip_stage ? STAGE_BYTES : 0, s);
 }
 
 // server mode: tile height 4, pushes along columns and rows
@@ -2246,12 +2424,62 @@ cudaError_t launch_begin_round(const Params &P, cudaStream_t s) {
 
 int worker_warps_per_block() { return WORKER_WARPS; }
 
-cudaError_t worker_occupancy(int tile_h, int *blocks_per_sm) {
+cudaError_t worker_occupancy(int tile_h, int *blocks_per_sm, bool staged) {
+    const size_t dyn = staged ? STAGE_BYTES : 0;
     if (tile_h == 4)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<4, 0, false, false>,
-                                                             WORKER_WARPS * 32, 0);
+                                                             WORKER_WARPS * 32, dyn);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, worker_kernel<8, 0, false, false>,
-                                                         WORKER_WARPS * 32, 0);
+                                                         WORKER_WARPS * 32, dyn);
+}
+
+// Tensor maps for staged strip loads, one per instance (its planes as a 3-D
+// array: pitch x rows x N_INST_PLANES, box STAGE_BOX_W x BFS_ROWS x
+// STAGE_INST_PLANES) and one per image (pitch x rows x N_IMG_PLANES, box
+// STAGE_BOX_W x BFS_ROWS x N_IMG_PLANES).  Reads outside a plane fill zeros.
+// The row pitch is a multiple of 32 elements, so every stride is a multiple of
+// 16 bytes, as the copies require.
+bool encode_plane_maps(unsigned char *host_out, const int32_t *inst_base, const int32_t *img_base, int n_inst,
+                       const int64_t *plane_off, const int *inst_image, int n_images, const int64_t *img_off,
+                       const int *rows, const int *pitch) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        (void)cudaGetLastError();
+    });
+    if (!encode) return false;
+    auto one = [&](unsigned char *dst, const int32_t *base, int r, int p, int planes, int box_planes) {
+        if (p % TILE_W != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+        CUtensorMap m;
+        const cuuint64_t dims[3] = {(cuuint64_t)p, (cuuint64_t)r, (cuuint64_t)planes};
+        const cuuint64_t strides[2] = {(cuuint64_t)p * 4, (cuuint64_t)p * r * 4};
+        const cuuint32_t box[3] = {(cuuint32_t)STAGE_BOX_W, (cuuint32_t)BFS_ROWS, (cuuint32_t)box_planes};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        const CUresult rc = encode(&m, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, const_cast<int32_t *>(base), dims, strides,
+                                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (rc != CUDA_SUCCESS) return false;
+        static_assert(sizeof(CUtensorMap) == TMAP_BYTES, "one tensor map per TMAP_BYTES");
+        std::memcpy(dst, &m, sizeof(m));
+        return true;
+    };
+    for (int i = 0; i < n_inst; ++i) {
+        const int im = inst_image[i];
+        if (!one(host_out + (size_t)i * TMAP_BYTES, inst_base + plane_off[i], rows[im], pitch[im], N_INST_PLANES,
+                 STAGE_INST_PLANES))
+            return false;
+    }
+    for (int im = 0; im < n_images; ++im)
+        if (!one(host_out + (size_t)(n_inst + im) * TMAP_BYTES, img_base + img_off[im], rows[im], pitch[im],
+                 N_IMG_PLANES, N_IMG_PLANES))
+            return false;
+    return true;
 }
 
 }  // namespace pmf

@@ -72,12 +72,23 @@ def test_uneven_subset_covers_every_size():
     assert len(firsts) == len(inputs.UNEVEN_SIZES)
 
 
-def test_supergraph_480x320_all_500_solves_at_bench_configuration(P):
+@pytest.fixture(scope="module")
+def supergraph_oracle():
     wl = inputs.supergraph_480x320()
-    plan = autotune.bench_plan(wl)
-    gpu = _solve_plan(P, wl, plan)
     ora = oracle.solve_workload(wl)
     assert sum(len(f) for f, _ in ora) == 500
+    return wl, ora
+
+
+@pytest.mark.parametrize("strip_stage", [0, 1])
+def test_supergraph_480x320_all_500_solves_at_bench_configuration(P, supergraph_oracle, strip_stage):
+    """strip_stage 0: the benchmark's own plan and knobs; 1: the same with the
+    relabel strips' first visits loading through tensor copies."""
+    wl, ora = supergraph_oracle
+    plan = autotune.bench_plan(wl)
+    if strip_stage:
+        plan = dict(plan, strip_stage=strip_stage)
+    gpu = _solve_plan(P, wl, plan)
     _compare(gpu, ora, range(len(wl.instances)))
     _invariants(gpu)
 

@@ -41,11 +41,14 @@ SHAPES = [(1, 1), (1, 7), (7, 1), (3, 5), (8, 32), (9, 33), (16, 31), (17, 65), 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("tile_h", [4, 8])
 @pytest.mark.parametrize("push_order", [0, 1])
-def test_random_small_grids(pmf, shape, tile_h, push_order):
+@pytest.mark.parametrize("strip_stage", [-1, 1])
+def test_random_small_grids(pmf, shape, tile_h, push_order, strip_stage):
+    """strip_stage 1: relabel strips' first visits load through tensor copies
+    (box columns from -4 at the left border, rows past the plane zero-filled)."""
     H, W = shape
     rng = np.random.default_rng(H * 1000 + W)
     wl = inputs.random_grid(H, W, rng, wmax=20, tmax=40, p_zero=0.2, n_lambda=4, lam_max=30)
-    check_workload(pmf, wl, tile_h=tile_h, push_order=push_order)
+    check_workload(pmf, wl, tile_h=tile_h, push_order=push_order, strip_stage=strip_stage)
 
 
 @pytest.mark.parametrize("case", ["repeated", "zero-slope", "from-zero"])
@@ -117,7 +120,7 @@ def test_fuzz_shapes_knobs_and_schedules(pmf, case):
     """Seeded random instances: grid shape (1 to 90 a side), capacity ranges
     and share of zero capacities, schedule length, batch size (1 to 4
     instances on up to 2 images), and solver knobs (tile height, push order,
-    sweeps, relabel cadence, label slack, grid size).  Flows and masks must
+    sweeps, relabel cadence, label slack, grid size, strip loads).  Flows and masks must
     equal the oracle's bit for bit."""
     rng = np.random.default_rng(7000 + case)
     wl = inputs.Workload(f"fuzz{case}")
@@ -137,4 +140,5 @@ def test_fuzz_shapes_knobs_and_schedules(pmf, case):
     knobs = dict(tile_h=int(rng.choice([4, 8])), push_order=int(rng.integers(0, 2)),
                  sweeps=int(rng.choice([1, 2, 4, 8, 16])), relabel_every=int(rng.choice([50, 200, 800, 3200])),
                  label_slack=int(rng.choice([-1, 1, 4, 16])), grid_blocks=int(rng.choice([0, 1, 7, 64])))
+    knobs["strip_stage"] = int(rng.choice([-1, 1]))
     check_workload(pmf, wl, **knobs)

@@ -177,6 +177,7 @@ def test_fuzz_mixed_sides_and_swapped_chains(P, case):
     knobs = dict(tile_h=int(rng.choice([4, 8])), push_order=int(rng.integers(0, 2)),
                  sweeps=int(rng.choice([1, 2, 4, 8, 16])), relabel_every=int(rng.choice([50, 200, 800, 1600])),
                  label_slack=int(rng.choice([0, 2, 4, 16])))
+    knobs["strip_stage"] = int(rng.choice([-1, 1]))
     b = P.batch_from_workload(flat, **knobs)
     for j, kind in enumerate(kinds):
         if kind:
