@@ -232,7 +232,7 @@ def run_ours(args, rank, world, dev):
                                  ("relabel_every", args.relabel_every), ("label_slack", args.label_slack),
                                  ("push_order", args.push_order), ("relabel_extra", args.relabel_extra),
                                  ("poll_ns", args.poll_ns), ("blocks_per_sm", args.blocks_per_sm),
-                                 ("strip_stage", args.strip_stage)) if v}
+                                 ("relabel_reach", args.relabel_reach), ("strip_stage", args.strip_stage)) if v}
     from paper_1509_06004_b300 import autotune
     m = min(len(i.lambdas) for i in wl.instances)
     plan, tuning, mode_probe = resolve_mode(args, wl, dev, tuning0)
@@ -310,7 +310,8 @@ def run_ours(args, rank, world, dev):
         "config": dict(describe(wl_whole, args.mode), tile=f"30x{tile_px // 30} (+2 mirrored columns)",
                        instances_launched=len(wl.instances),
                        sweeps=b.tuning()["sweeps"], relabel_every_pct=b.tuning()["relabel_every"],
-                       relabel_extra=b.tuning()["relabel_extra"], poll_ns=b.tuning()["poll_ns"],
+                       relabel_extra=b.tuning()["relabel_extra"], relabel_reach=b.tuning()["relabel_reach"],
+                       poll_ns=b.tuning()["poll_ns"],
                        label_slack=b.tuning()["label_slack"], blocks_per_sm=b.tuning()["blocks_per_sm"] or "occupancy",
                        strip_loads="tensor copies" if b.tuning()["strip_stage"] == 1 else "per lane",
                        l2="flushed between timed steps (512 MB write)",
@@ -637,6 +638,7 @@ def main(argv=None):
     ap.add_argument("--sweeps", type=int, default=0)
     ap.add_argument("--relabel-every", type=int, default=0)
     ap.add_argument("--relabel-extra", type=int, default=0)
+    ap.add_argument("--relabel-reach", type=int, default=0)
     ap.add_argument("--poll-ns", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--label-slack", type=int, default=0)

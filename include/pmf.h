@@ -121,6 +121,11 @@ typedef struct {
     int32_t relabel_extra;   /* tile visits every push/relabel phase may spend on top
                                 of relabel_every% of its tiles (default 0): more room
                                 for phases that start with few active tiles */
+    int32_t relabel_reach;   /* a push/relabel phase may spend at least relabel_reach% of
+                                the largest finite distance of the last global relabel
+                                in tile visits (default 0 = no such floor): phases that
+                                start with few active tiles get room to carry their
+                                excess that far before the next global relabel */
     int32_t strip_stage;     /* 1 = a relabel strip's first visit of a global relabel
                                 loads its 32 rows of state and capacities with two
                                 tensor copies into shared memory (one buffer per

@@ -19,6 +19,8 @@ instance count and schedule length:
   state, or along columns and rows), ``sweeps`` (push/relabel sweeps per tile visit),
   ``relabel_every`` (visit budget of a push/relabel phase, percent of its
   tiles), ``relabel_extra`` (visits added to every phase's budget),
+  ``relabel_reach`` (a phase's budget floor, percent of the last relabel's
+  largest distance),
   ``label_slack`` (parking threshold above the last exact distance),
   ``poll_ns`` (longest sleep of an idle warp between polls of its queue slot) and
   ``blocks_per_sm`` (4 resident blocks, or 3 with more registers each).
@@ -40,7 +42,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_PATH = os.path.join(HERE, "tuned.json")
 
 DEFAULTS = {"tile_h": 4, "sweeps": 8, "relabel_every": 800, "label_slack": 16, "push_order": 0, "relabel_extra": 0,
-            "poll_ns": 256, "blocks_per_sm": 0, "strip_stage": -1}
+            "poll_ns": 256, "blocks_per_sm": 0, "relabel_reach": 0, "strip_stage": -1}
 SPACE = {
     "tile_h": [4, 8],
     "push_order": [0, 1],
@@ -48,6 +50,7 @@ SPACE = {
     "relabel_every": [200, 400, 800, 1600, 3200, 6400],
     "label_slack": [2, 4, 8, 16, 32],
     "relabel_extra": [0, 64, 256, 1024],
+    "relabel_reach": [0, 400, 800],
     "poll_ns": [256, 1024, 4096],
     # 0: the occupancy (4 blocks per SM at tile height 4); 3: the build with
     # the fourth block's registers (no spills)

@@ -248,6 +248,7 @@ void apply_defaults(pmf_tuning *t) {
     if (t->label_slack < 0) t->label_slack = -1;
     if (t->push_order != 1) t->push_order = 0;
     if (t->relabel_extra < 0) t->relabel_extra = 0;
+    if (t->relabel_reach < 0) t->relabel_reach = 0;
     if (t->strip_stage != 1) t->strip_stage = -1;
 }
 
@@ -712,6 +713,7 @@ static pmf_status solve_impl(pmf_batch *b, const int32_t *lambdas, const int32_t
     b->P.chain_push = b->tune.push_order;
     b->P.relabel_pct = b->tune.relabel_every;
     b->P.relabel_extra = b->tune.relabel_extra;
+    b->P.relabel_reach = b->tune.relabel_reach;
     b->P.any_sink_side = 0;
     for (int i = 0; i < b->desc.n_inst; ++i) b->P.any_sink_side |= b->dinst[i].slope_side != 0;
     b->P.max_visits_per_tile = b->tune.max_visits_per_tile;
@@ -1182,6 +1184,7 @@ pmf_status pmf_server_start(pmf_server *s, double max_seconds) {
     P.chain_push = 1;
     P.relabel_pct = s->tune.relabel_every;
     P.relabel_extra = s->tune.relabel_extra;
+    P.relabel_reach = s->tune.relabel_reach;
     P.max_visits_per_tile = s->tune.max_visits_per_tile;
     P.max_ns = (long long)(max_seconds * 1e9);
     std::memset(s->mb, 0, sizeof(Mailbox));

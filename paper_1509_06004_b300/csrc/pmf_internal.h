@@ -177,6 +177,7 @@ struct Params {
                                  // and wait for their parent)
     int32_t relabel_pct, tile_h;
     int32_t relabel_extra;       // visits added to every phase's budget
+    int32_t relabel_reach;       // a phase's budget is at least relabel_reach% of the last relabel's largest distance
     int32_t any_sink_side;       // some instance's sink capacities fall with lambda (slope_side 1)
     int32_t wide_regs;           // tile height 4 on 1-3 blocks per SM: the build with more registers
     int32_t poll_ns, label_slack;

@@ -554,9 +554,14 @@ __device__ bool transition_once(const Params &P, int inst, int *other) {
         // a push/relabel phase may spend relabel_pct% of the tiles it starts
         // with (at least 4 visits) before the next global relabel: when only
         // a few tiles hold active pixels, stranded excess is otherwise pushed
-        // back and forth between them long before a relabel removes it
-        const long long bud = (long long)P.relabel_pct * n / 100 + P.relabel_extra;
-        S->pr_budget = (int)(bud < 4 ? 4 : bud);
+        // back and forth between them long before a relabel removes it.  With
+        // relabel_reach set, the budget is at least that percentage of the
+        // largest exact distance of the last relabel: the excess left in the
+        // long tail of a hard step then gets visits enough to travel that far
+        // instead of a global relabel every few hundred visits
+        long long bud = (long long)P.relabel_pct * n / 100 + P.relabel_extra;
+        bud = max(bud, (long long)P.relabel_reach * S->dmax / 100);
+        S->pr_budget = (int)(bud < 4 ? 4 : (bud > (1LL << 30) ? (1LL << 30) : bud));
         // labels far above every exact distance of the last relabel belong
         // to excess that keeps climbing without reaching t: park it until
         // the next relabel (which re-activates whatever can still reach t)

@@ -72,7 +72,8 @@ class Tuning(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("trace", ctypes.c_int32),
                 ("poll_ns", ctypes.c_int32), ("label_slack", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("push_order", ctypes.c_int32),
-                ("relabel_extra", ctypes.c_int32), ("strip_stage", ctypes.c_int32)]
+                ("relabel_extra", ctypes.c_int32), ("relabel_reach", ctypes.c_int32),
+                ("strip_stage", ctypes.c_int32)]
 
 
 class ServerDesc(ctypes.Structure):

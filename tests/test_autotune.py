@@ -18,7 +18,7 @@ def test_coordinate_descent_finds_separable_minimum():
     wl = inputs.single_maxflow_64()
     wl.instances[0].lambdas = np.arange(1, 13, dtype=np.int32)   # 12 lambdas: segments 1..12
     target = {"segments": 4, "tile_h": 8, "push_order": 1, "sweeps": 16, "relabel_every": 400, "label_slack": 32,
-              "relabel_extra": 256, "poll_ns": 1024, "blocks_per_sm": 3}
+              "relabel_extra": 256, "relabel_reach": 800, "poll_ns": 1024, "blocks_per_sm": 3}
 
     def cost(w, p, k):
         assert p["interleave"] == 1 or p["segments"] == 1

@@ -120,7 +120,7 @@ def test_fuzz_shapes_knobs_and_schedules(pmf, case):
     """Seeded random instances: grid shape (1 to 90 a side), capacity ranges
     and share of zero capacities, schedule length, batch size (1 to 4
     instances on up to 2 images), and solver knobs (tile height, push order,
-    sweeps, relabel cadence, label slack, grid size, strip loads).  Flows and masks must
+    sweeps, relabel cadence, label slack, grid size, strip loads, budget floor).  Flows and masks must
     equal the oracle's bit for bit."""
     rng = np.random.default_rng(7000 + case)
     wl = inputs.Workload(f"fuzz{case}")
@@ -141,4 +141,5 @@ def test_fuzz_shapes_knobs_and_schedules(pmf, case):
                  sweeps=int(rng.choice([1, 2, 4, 8, 16])), relabel_every=int(rng.choice([50, 200, 800, 3200])),
                  label_slack=int(rng.choice([-1, 1, 4, 16])), grid_blocks=int(rng.choice([0, 1, 7, 64])))
     knobs["strip_stage"] = int(rng.choice([-1, 1]))
+    knobs["relabel_reach"] = int(rng.choice([0, 400, 800, 3200]))
     check_workload(pmf, wl, **knobs)

@@ -178,6 +178,7 @@ def test_fuzz_mixed_sides_and_swapped_chains(P, case):
                  sweeps=int(rng.choice([1, 2, 4, 8, 16])), relabel_every=int(rng.choice([50, 200, 800, 1600])),
                  label_slack=int(rng.choice([0, 2, 4, 16])))
     knobs["strip_stage"] = int(rng.choice([-1, 1]))
+    knobs["relabel_reach"] = int(rng.choice([0, 400, 800]))
     b = P.batch_from_workload(flat, **knobs)
     for j, kind in enumerate(kinds):
         if kind:
