@@ -47,6 +47,8 @@ WORKLOADS = {
     "supergraph-480x320-15seeds": lambda seed: _first_instances(inputs.supergraph_480x320(seed=seed), 15),
     "parametric-320x240": lambda seed: inputs.parametric_320x240(seed=seed),
     "uneven-64": lambda seed: inputs.uneven_batch(first_seed=64 * seed),
+    # its first 8 images x 8 seeds (the small case its profiles are taken on)
+    "uneven-64-8images": lambda seed: _first_instances(inputs.uneven_batch(first_seed=64 * seed), 64),
     "single-64x64": lambda seed: inputs.single_maxflow_64(seed=seed),
 }
 

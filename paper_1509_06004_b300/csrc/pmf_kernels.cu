@@ -618,7 +618,13 @@ __device__ void transition(const Params &P, int inst) {
 // warp instead of queueing it: chains of dependent visits then stay on an SM
 // whose caches hold the code and the neighbourhood (the queue otherwise hands
 // an item to the warp that has been idle longest).  Returns -1 otherwise.
+// OOL: the phase change is called out of line (see worker_kernel).
 template <bool SV>
+__device__ __noinline__ void transition_ool(const Params &P, int inst) {
+    transition<SV>(P, inst);
+}
+
+template <bool SV, bool OOL = false>
 __device__ int finish(const Params &P, int g, int inst, int phase, bool requeue, unsigned nb,
                       const DevInst &D, bool keep) {
     const int lane = threadIdx.x & 31;
@@ -694,7 +700,10 @@ __device__ int finish(const Params &P, int g, int inst, int phase, bool requeue,
         int dummy;
         if (slot_wait(P, slot, true, &dummy)) *slot = item;
     }
-    if (trans) transition<SV>(P, inst);  // only when k == 0, so nothing is kept
+    if (trans) {                         // only when k == 0, so nothing is kept
+        if constexpr (OOL) transition_ool<SV>(P, inst);
+        else transition<SV>(P, inst);
+    }
     return kept;
 }
 
@@ -1190,6 +1199,11 @@ __device__ void warm_visit(const Params &P, int g, int inst, const DevInst &D, i
         if (sent) atomicAdd(&P.ist[inst].flow, (unsigned long long)sent);
         atomicAdd(&P.ist[inst].warm_visits, 1ULL);
     }
+}
+
+template <int TH, bool SINK, bool SV>
+__device__ __noinline__ void warm_visit_ool(const Params &P, int g, int inst, const DevInst &D, int kcur) {
+    warm_visit<TH, SINK, SV>(P, g, inst, D, kcur);
 }
 
 // --------------------------------------------------------------------------
@@ -1863,6 +1877,12 @@ constexpr int WORKER_WARPS = 4;
 template <int TH, int PO, bool SINK, bool SV, int MINB = (TH == 4 ? 4 : 2)>
 __global__ void __launch_bounds__(WORKER_WARPS * 32, MINB) worker_kernel(const __grid_constant__ Params P) {
     __shared__ WarpSmem<TH> smem[WORKER_WARPS];
+    // In the 4-block builds (128 registers) the rarely run warm-start pass and
+    // phase change are called out of line, which keeps the hot loop's code
+    // compact (instruction fetch was the top stall of the uneven batch): the
+    // uneven batch runs 2 % faster although more registers spill.  The wider
+    // builds keep them inline (out of line cost them 5-6 %).
+    constexpr bool OOL = MINB == 4 && !SV;
     // staged strip loads: the block's buffer (dynamic shared memory, present
     // only when P.strip_stage is set) and its barrier
     extern __shared__ __align__(128) int32_t stage_buf[];
@@ -1936,7 +1956,10 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, MINB) worker_kernel(const _
             bfs_visit<TH, false, SV>(P, S, SS, g, inst, D, epoch, k, requeue, nb);
         else if (status == PMF_OK && phase == PH_FWD && !stray)
             bfs_visit<TH, true, SV>(P, S, SS, g, inst, D, epoch, k, requeue, nb);
-        else if (status == PMF_OK && phase == PH_WARM && !stray) warm_visit<TH, SINK, SV>(P, g, inst, D, k);
+        else if (status == PMF_OK && phase == PH_WARM && !stray) {
+            if constexpr (OOL) warm_visit_ool<TH, SINK, SV>(P, g, inst, D, k);
+            else warm_visit<TH, SINK, SV>(P, g, inst, D, k);
+        }
         else if (status == PMF_OK && phase == PH_COPY && !stray) copy_visit<TH, SV>(P, g, inst, D);
         else if (SV && phase == PH_SETUP && !stray) setup_visit<TH>(P, g, inst, D);
         __threadfence();
@@ -1947,7 +1970,7 @@ __global__ void __launch_bounds__(WORKER_WARPS * 32, MINB) worker_kernel(const _
             t0 = t1;
         }
         // in host-polled rounds every new item waits for the next round
-        next = finish<SV>(P, g, inst, phase, requeue, nb, D, round_mode == 0);
+        next = finish<SV, OOL>(P, g, inst, phase, requeue, nb, D, round_mode == 0);
         if (prof) { const unsigned long long t1 = gtime_ns(); tfin += t1 - t0; t0 = t1; }
     }
     if (prof && lane == 0) {
